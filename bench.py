@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark of the molecule-agent step engine on B300.
+
+Default workload: the MAPK-like cascade with 1,000,000 agents in a 10 um cube
+(9 species, 12 bind/release reactions, dt = 1 us), seed 12.  One "step" is
+one full pass of the hot path over every agent: first-order events, Brownian
+move, grid build (histogram, scan, scatter), 27-cell proposals, acceptance
+and births.  The state (about 86 MB) fits in the 126 MB L2, so L2 is flushed
+(a 256 MB write) between timed steps and each step is timed on its own with
+CUDA events on the engine's stream.
+
+Prints one JSON line.  `value` = molecule-steps/s summed over ranks (each rank
+runs an independent replica: weak scaling).  `--impl reference` times the CPU
+oracle (the serial simulator under oracle/) on a bounded sample instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "molecule-steps/s @1M agents (%HBM roofline); batched vs serial sweep; p50/p99"
+UNIT = "molecule-steps/s"
+# per-kernel bytes each launch must move per unit (agent or cell) in this
+# design; the step as a whole must read and rewrite the 20-byte agent record
+STEP_BYTES_PER_AGENT = 40
+KERNEL_BYTES = {"k_move": (44, "agent"), "k_scan": (12, "cell"), "k_scatter": (56, "agent"),
+                "k_propose": (24, "agent"), "k_accept": (4, "agent"), "k_finalize": (0, "agent")}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["cascade", "nuclear", "toy"], default="cascade")
+    p.add_argument("--agents", type=int, default=0, help="override the agent count")
+    p.add_argument("--profile-steps", type=int, default=50)
+    p.add_argument("--no-flush", action="store_true", help="do not flush L2 between steps")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    import workloads as W
+    if args.workload == "cascade":
+        n = args.agents or 1_000_000
+        return W.mapk(n), W.MAPK_SEED, f"cascade_{n}"
+    if args.workload == "nuclear":
+        n = args.agents or 4_000_000
+        return W.nuclear(n), W.NUCLEAR_SEED, f"two_compartment_{n}"
+    return W.toy(), W.TOY_SEED, "toy_5000"
+
+
+def config_of(args, model, name, extra=None):
+    c = {"workload": name, "agents": model.n_agents, "species": len(model.species),
+         "reactions": len(model.reactions), "compartments": len(model.compartments),
+         "dt_s": model.dt_s, "position_unit_nm": model.unit_nm,
+         "l2": "no flush" if args.no_flush else "flushed between timed steps (256 MB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def molecules(counts, model):
+    n_sp, n_c = len(model.species), len(model.compartments)
+    free = int(counts[: n_sp * n_c].sum())
+    bound = int(counts[n_sp * n_c: -1].sum())
+    return free + 2 * bound
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
+    kernel source is unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2606_14603_b300", "csrc", "kernels.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            f = line.split()
+            if len(f) >= 5 and not line.startswith("#") and f[0] == kernel and f[1] == sha:
+                return float(f[2]), float(f[3]), f[4]
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank):
+    """The oracle on the host cores, on a bounded sample of the same workload."""
+    import oracle
+    model, seed, name = workload(args)
+    sim = oracle.OracleSim(model, seed)
+    t0 = time.perf_counter()
+    sim.step(1)
+    est = time.perf_counter() - t0
+    budget = 90.0
+    warm = min(args.warmup, max(0, int(10.0 / max(est, 1e-6))))
+    sim.step(warm)
+    steps = max(1, min(args.steps, int(budget / max(est, 1e-6))))
+    n0 = molecules(sim.counts(), model)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    el = time.perf_counter() - t0
+    n1 = molecules(sim.counts(), model)
+    value = 0.5 * (n0 + n1) * steps / el
+    sample = f"{name}: {steps} oracle steps after {1 + warm} untimed, single thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": 1 + warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config_of(args, model, name),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(model, seed, name, seconds=12.0):
+    import oracle
+    sim = oracle.OracleSim(model, seed)
+    t0 = time.perf_counter()
+    steps = 0
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        n += molecules(sim.counts(), model) if steps == 0 else 0
+        sim.step(1)
+        steps += 1
+    el = time.perf_counter() - t0
+    n = molecules(sim.counts(), model)
+    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{name}: the first {steps} steps from t = 0, serial oracle, one thread"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2606_14603_b300 import build as engine_build
+    engine_build.build()
+    import paper_2606_14603_b300 as A
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    model, seed, name = workload(args)
+    seed = seed + rank                      # independent replicas
+    stream = torch.cuda.Stream()
+    sim = A.Sim(model, seed, stream=stream)
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # warm-up (untimed)
+    sim.step(args.warmup)
+    sim.sync()
+    n_before = molecules(sim.counts(), model)
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(K):
+            if flush is not None:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+            starts[k].record(stream)
+            sim.step(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    sim.sync()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    n_after = molecules(sim.counts(), model)
+    mol_steps = 0.5 * (n_before + n_after) * K
+    if dist:
+        t = torch.tensor([total_ms, mol_steps], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, mol_steps_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_max, mol_steps_all = total_ms, mol_steps
+    value = mol_steps_all / (total_ms_max / 1e3)
+    per_step = sorted(step_ms)
+
+    # per-kernel breakdown with the same L2 state (flushed before each step)
+    prof = {k: 0.0 for k in KERNEL_BYTES}
+    P = max(1, args.profile_steps)
+    for _ in range(P):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        for k, v in sim.profile_step(1).items():
+            prof[k] += v
+    tot = sum(prof.values())
+    share = {k: v / tot for k, v in prof.items()}
+    dom = max(prof, key=prof.get)
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    n_agents = 0.5 * (n_before + n_after)
+    sd = None
+    # cells of the simulation grid for per-cell kernels
+    import workloads as W  # noqa: F401
+    gx = None
+    bpu, unit_name = KERNEL_BYTES[dom]
+    ext = model.compartments[0].size_um * 1000 / model.unit_nm
+    cell_log2 = int(os.environ.get("ABM_CELL_LOG2", "0"))
+    units = n_agents
+    if unit_name == "cell":
+        units = (int(round(ext)) // 1024 + 1) ** 3
+    dom_ms = prof[dom] / P
+    achieved = bpu * units / (dom_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dom)
+    step_ms_avg = total_ms / K
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic[0] if traffic else None,
+            "bytes_per_unit": bpu, "units_per_launch": units, "unit_of_work": unit_name,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.4 TB/s",
+            "kernel_ms": dom_ms}
+    step_roof = {"bytes_per_molecule_step": STEP_BYTES_PER_AGENT,
+                 "achieved_gbs": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9,
+                 "frac": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9 / hbm}
+
+    # end to end: create from host structs, K steps each followed by a
+    # device-to-host read of the counts vector
+    e2e = None
+    if not args.no_e2e:
+        Ke = max(1, min(K, 500))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = A.Sim(model, seed, stream=stream)
+        cvec = None
+        for _ in range(Ke):
+            s2.step(1)
+            cvec = s2.counts()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        s2.close()
+        n_counts = len(cvec)
+        model_bytes = len(model.species) * 48 + len(model.reactions) * 48 + len(model.compartments) * 48 + 2 * 65536
+        e2e = {"value": molecules(cvec, model) * Ke / el, "unit": UNIT,
+               "h2d_bytes_per_step": model_bytes / Ke, "d2h_bytes_per_step": 8 * n_counts,
+               "steps": Ke, "includes": "abm_create (model upload, device-side placement) + per step "
+                                       "abm_step + abm_counts read back to host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(model, seed, name)
+
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": config_of(args, model, name, {"parallelism": f"replicas x{world}",
+                                                    "seed": seed - rank}),
+            "p50_step_ms": per_step[len(per_step) // 2], "p99_step_ms": per_step[int(0.99 * (len(per_step) - 1))],
+            "roofline": roof, "step_roofline": step_roof,
+            "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
+            "gpu_launches": A.N_STEP_KERNELS * K, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clocks, "wall_s_timed_region": wall}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

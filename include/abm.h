@@ -1,0 +1,213 @@
+/*
+ * abm.h — C ABI of the B300 molecule-agent step engine.
+ *
+ * The engine advances a 3D agent-based simulation in which every molecule is
+ * an agent (paper, Sec. 2 "Materials and Methods": molecules are spheres that
+ * diffuse, bind substrates or inhibitors by spatial proximity, release
+ * products after a turnover time, are produced by expressors at a fixed rate
+ * and move between compartments at translocation rates).  The inputs follow
+ * the paper's list of what a model needs (Sec. 2, footnote 1): the simulated
+ * volume, initial amounts, per-molecule properties (diffusion from molecular
+ * size), reactions with partners, rates and products, compartment volumes
+ * and translocation rates, and expression rates.
+ *
+ * One step of every simulation runs: first-order events (release of bound
+ * complexes, conversion/degradation, expression), a Brownian move with
+ * reflecting walls, rejecting spherical walls and membrane crossing, a cell
+ * grid rebuilt by histogram / exclusive scan / scatter, a 27-cell proximity
+ * proposal, a nearest-partner handshake (atomicMin on a packed (dist^2, id)
+ * key), reaction application and births.  All state is integer; all
+ * randomness is Philox4x32-10 keyed by (seed, step, agent id), so a run is
+ * bit-reproducible and independent of storage order.
+ *
+ * Conventions for every call:
+ *  - Return value: an abm_status.  After any failure other than ABM_EINVAL
+ *    at creation, the handle is in a failed state: every call except
+ *    abm_*_last_error and abm_*_destroy returns ABM_ESTATE.
+ *  - Host pointers are read during the call only (copied); the caller keeps
+ *    ownership.  Device memory passed as `arena` and the `stream` belong to
+ *    the caller and must outlive the handle.
+ *  - abm_*_step only enqueues work on the stream and returns.  Errors found
+ *    on the device (capacity exceeded, bounded waits timed out) are sticky
+ *    and reported by the next synchronising call (counts, digest, dump,
+ *    sync).
+ *  - Not thread-safe: one host thread per handle at a time.
+ */
+#ifndef ABM_H
+#define ABM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ABM_OK = 0,
+    ABM_EINVAL = -1,     /* invalid model or argument; nothing was created */
+    ABM_ENOMEM = -2,     /* device allocation failed or arena too small    */
+    ABM_ECUDA = -3,      /* a CUDA runtime call failed                     */
+    ABM_ETIMEOUT = -4,   /* a bounded device-side wait gave up             */
+    ABM_ECAPACITY = -5,  /* agents, cells, births or sims exceed capacity  */
+    ABM_EDEVICE = -6,    /* no usable CUDA device (sm_103 required)        */
+    ABM_ESTATE = -7      /* handle already failed, or bad sim index        */
+} abm_status;
+
+enum { ABM_CONVERT = 0, ABM_BIND = 1 };
+enum { ABM_CUBE = 0, ABM_SPHERE = 1 };
+
+/* A molecular species (paper Sec. 2: molecule classes and per-species
+ * properties).  D_um2_s is the Stokes-Einstein diffusion coefficient the
+ * caller derived from the molecular weight; 0 makes an immobile agent (gene
+ * site).  An expressor is a species with p_emit > 0. */
+typedef struct {
+    uint32_t initial_count;  /* agents placed at creation                  */
+    double   D_um2_s;        /* diffusion coefficient, um^2/s, >= 0        */
+    int32_t  compartment;    /* compartment of the initial agents          */
+    double   p_cross;        /* probability per attempted crossing, [0,1]  */
+    double   p_uni;          /* first-order conversion per step, [0,1]     */
+    int32_t  uni_to;         /* product of the conversion; -1 = death      */
+    double   p_emit;         /* birth probability per step, [0,1]          */
+    int32_t  emit_species;   /* species of the child; -1 = none            */
+} abm_species;
+
+/* A bimolecular reaction (paper Sec. 2: interacting partners, rates and
+ * products).  Agent of species a proposes to agent of species b when they
+ * are within radius_nm; CONVERT changes both at once, BIND forms a complex
+ * that releases (prod_a, prod_b) with p_release per step (the turnover time).
+ * Each unordered species pair has at most one reaction; a != b. */
+typedef struct {
+    int32_t a, b;
+    int32_t kind;            /* ABM_CONVERT | ABM_BIND                     */
+    int32_t prod_a, prod_b;  /* species afterwards; -1 = the agent dies    */
+    double  radius_nm;       /* contact radius (> 0, <= the grid cell)     */
+    double  p_bind;          /* Bernoulli per eligible contact, [0,1]      */
+    double  p_release;       /* BIND only: per step, [0,1]                 */
+} abm_reaction;
+
+/* Compartment 0 is the root (a cube of edge size_um or a sphere of diameter
+ * size_um).  Compartments 1..3 are spheres (diameter size_um) inside the
+ * root, centred at the root centre plus center_um, not overlapping (the
+ * nucleus of paper Sec. 3.4). */
+typedef struct {
+    int32_t shape;           /* ABM_CUBE (root only) | ABM_SPHERE          */
+    double  size_um;
+    int32_t parent;          /* -1 for the root, 0 for a child             */
+    double  center_um[3];
+} abm_compartment;
+
+typedef struct {
+    const abm_species*     species;       /* n_species in [1, 64]          */
+    uint32_t               n_species;
+    const abm_reaction*    reactions;     /* n_reactions in [0, 255]       */
+    uint32_t               n_reactions;
+    const abm_compartment* compartments;  /* n_compartments in [1, 4]      */
+    uint32_t               n_compartments;
+    double                 dt_s;          /* time step, > 0                */
+    double                 unit_nm;       /* position quantum, > 0 (0.1)   */
+} abm_model;
+
+/* Options of a single simulation.  Zero-initialise and set what you need. */
+typedef struct {
+    uint64_t       capacity_agents;  /* 0 = initial count * 1.25 + 65536  */
+    uint32_t       cell_log2;        /* grid cell = 2^k units; 0 = auto    */
+    uint32_t       births_per_step;  /* 0 = 8192 (also the maximum)        */
+    void*          arena;            /* device memory, or NULL = library   */
+    size_t         arena_bytes;
+    void*          stream;           /* cudaStream_t, or NULL = library    */
+    const int16_t* ncdf_table;       /* 65536 entries or NULL = built in   */
+} abm_options;
+
+/* Options of a batch of simulations stepped together. */
+typedef struct {
+    uint64_t       capacity_agents;  /* slots shared by all sims (> 0)     */
+    uint64_t       capacity_cells;   /* grid cells shared by all sims      */
+    uint32_t       max_sims;         /* 1..4096                            */
+    uint32_t       births_per_step;  /* 0 = 8192 (also the maximum)        */
+    void*          arena;
+    size_t         arena_bytes;
+    void*          stream;
+    const int16_t* ncdf_table;
+} abm_batch_options;
+
+/* Layout of abm_*_counts output (uint64 each):
+ *   [n_species * n_compartments free agents, index species*n_comp + comp]
+ *   [n_reactions bound complexes][next_id]
+ * One dump record per agent (hidden partners of complexes included), sorted
+ * by id, 24 bytes: */
+typedef struct {
+    uint32_t id;
+    uint8_t  species, compartment;
+    uint8_t  flags;          /* 1 carrier of a complex, 2 hidden, 4 reactant a */
+    uint8_t  reaction;       /* 0xFF when free                             */
+    int32_t  x, y, z;        /* units of unit_nm; hidden: carrier's place  */
+    uint32_t partner;        /* 0xFFFFFFFF when free                       */
+} abm_record;
+
+/* ---------------- single simulation ---------------- */
+typedef struct abm_sim abm_sim;
+
+/* Bytes of device memory a simulation needs for these model and options
+ * (the arena must be 256-byte aligned).  Returns 0 for an invalid model. */
+size_t      abm_arena_bytes(const abm_model* model, const abm_options* opt);
+abm_status  abm_create(const abm_model* model, uint64_t seed, const abm_options* opt,
+                       abm_sim** out);
+abm_status  abm_step(abm_sim* sim, uint32_t n);
+abm_status  abm_counts(abm_sim* sim, uint64_t* out, size_t cap, size_t* n_out);
+abm_status  abm_digest(abm_sim* sim, uint64_t* out);
+abm_status  abm_dump(abm_sim* sim, abm_record* out, size_t cap, size_t* n_out);
+abm_status  abm_sync(abm_sim* sim);
+abm_status  abm_step_index(abm_sim* sim, uint32_t* out);
+const char* abm_last_error(const abm_sim* sim);
+void        abm_destroy(abm_sim* sim);        /* NULL-safe */
+
+/* ---------------- batch of simulations ---------------- */
+typedef struct abm_batch abm_batch;
+
+size_t      abm_batch_arena_bytes(const abm_batch_options* opt);
+abm_status  abm_batch_create(const abm_batch_options* opt, abm_batch** out);
+/* Admit a simulation between steps: validates the model, places its agents
+ * (on the device) and returns its slot in *sim_id.  cell_log2 as above.
+ * Synchronises the stream.  ABM_ECAPACITY if agents, cells or slots run out. */
+abm_status  abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed,
+                          uint32_t cell_log2, int32_t* sim_id);
+/* Retire a simulation: its agents are dropped by the next step's grid build
+ * and its slot, agents and cells become free for later admissions. */
+abm_status  abm_batch_remove(abm_batch* b, int32_t sim_id);
+abm_status  abm_batch_step(abm_batch* b, uint32_t n);
+abm_status  abm_batch_counts(abm_batch* b, int32_t sim_id, uint64_t* out, size_t cap,
+                             size_t* n_out);
+abm_status  abm_batch_digest(abm_batch* b, int32_t sim_id, uint64_t* out);
+abm_status  abm_batch_dump(abm_batch* b, int32_t sim_id, abm_record* out, size_t cap,
+                           size_t* n_out);
+abm_status  abm_batch_sync(abm_batch* b);
+abm_status  abm_batch_live_agents(abm_batch* b, uint64_t* out);  /* syncs */
+const char* abm_batch_last_error(const abm_batch* b);
+void        abm_batch_destroy(abm_batch* b);  /* NULL-safe */
+
+/* ---------------- profiling ---------------- */
+/* Runs n steps without the CUDA graph, with a CUDA event on the stream
+ * before and after each of the step's kernels, and writes the summed time of
+ * each kernel in milliseconds to kernel_ms[0..5] (n_kernels >= 6; names from
+ * abm_kernel_name).  Synchronous.  The state advances exactly as abm_step. */
+abm_status  abm_profile_step(abm_sim* sim, uint32_t n, float* kernel_ms, uint32_t n_kernels);
+abm_status  abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, uint32_t n_kernels);
+/* Name of step kernel k (0..5), or NULL. */
+const char* abm_kernel_name(uint32_t k);
+
+/* ---------------- building blocks (host or debug) ---------------- */
+/* The Gaussian inverse-CDF table the engine uses when none is given:
+ * Z[i] = round(4096 * inv_Phi((i + 1/2) / 65536)), host computation. */
+void        abm_ncdf_table(int16_t* out65536);
+/* Runs the engine's device Philox4x32-10 on n (counter, key) pairs given as
+ * host arrays ctr[4n], key[2n]; writes out[4n] (host).  Synchronous. */
+abm_status  abm_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                             size_t n);
+/* Library version string. */
+const char* abm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABM_H */

@@ -1,0 +1,920 @@
+// api.cu — host side of the C ABI (include/abm.h): model validation and
+// compilation to integers, arena layout, admission of simulations into a
+// batch, CUDA-graph capture of the step, and the observation calls.
+//
+// Physical-to-integer conversions follow one rule: evaluate left to right in
+// IEEE double, round half away from zero (llround).
+//   extent      cube: llround(edge_um * 1000 / unit_nm); sphere: 2 r with
+//               r = llround(diameter_um * 1000 / unit_nm / 2)
+//   M           llround(sqrt(2 D dt) * 1000 / unit_nm * 2^20)
+//   thresholds  floor(p * 2^32)
+//   radius      llround(radius_nm / unit_nm)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/abm.h"
+#include "engine.cuh"
+
+using namespace abm;
+
+namespace {
+
+constexpr int kTile = 4096;
+constexpr size_t kAlign = 256;
+
+// ------------------------------------------------------------------------
+// Built-in Gaussian table.  inv_Phi on the lower half by Newton's method on
+// Phi(x) - p (Phi from erfc), started from the rational approximation of
+// Abramowitz & Stegun 26.2.23; the upper half mirrors it.
+double normal_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+double inv_normal_lower(double p) {
+    const double t = std::sqrt(-2.0 * std::log(p));
+    double x = -(t - (2.515517 + 0.802853 * t + 0.010328 * t * t) /
+                         (1.0 + 1.432788 * t + 0.189269 * t * t + 0.001308 * t * t * t));
+    for (int it = 0; it < 100; it++) {
+        const double dens = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
+        const double step = (normal_cdf(x) - p) / dens;
+        x -= step;
+        if (std::fabs(step) <= 1e-16 * std::fabs(x)) break;
+    }
+    return x;
+}
+
+void build_table(int16_t* out) {
+    for (int i = 0; i < 32768; i++) {
+        const double q = inv_normal_lower((i + 0.5) / 65536.0);
+        const int16_t mag = (int16_t)std::floor(-4096.0 * q + 0.5);
+        out[i] = (int16_t)-mag;
+        out[65535 - i] = mag;
+    }
+}
+
+uint64_t threshold(double p) { return (uint64_t)std::floor(p * 4294967296.0); }
+bool prob_ok(double p) { return std::isfinite(p) && p >= 0.0 && p <= 1.0; }
+
+// ------------------------------------------------------------------------
+struct Compiled {
+    ModelDev dev;
+    SimDev geo;  // geometry part of the sim entry
+    int64_t Rmax = 0;
+    uint64_t n0 = 0;
+    uint32_t species_end[kMaxSpecies] = {};
+    double volume = 0;  // root volume in units^3
+};
+
+abm_status compile_model(const abm_model* m, Compiled* c, std::string* err) {
+    auto bad = [&](const char* msg) {
+        *err = msg;
+        return ABM_EINVAL;
+    };
+    if (!m) return bad("model is NULL");
+    if (!m->species || m->n_species < 1 || m->n_species > (uint32_t)kMaxSpecies)
+        return bad("n_species must be in [1, 64]");
+    if (m->n_reactions > (uint32_t)kMaxReactions || (m->n_reactions && !m->reactions))
+        return bad("n_reactions must be in [0, 255]");
+    if (!m->compartments || m->n_compartments < 1 || m->n_compartments > (uint32_t)kMaxComp)
+        return bad("n_compartments must be in [1, 4]");
+    const double dt = m->dt_s, unit = m->unit_nm;
+    if (!(std::isfinite(dt) && dt > 0) || !(std::isfinite(unit) && unit > 0))
+        return bad("dt_s and unit_nm must be positive");
+    std::memset(&c->dev, 0, sizeof(c->dev));
+    std::memset(&c->geo, 0, sizeof(c->geo));
+    std::memset(c->dev.rx_of, 0xFF, sizeof(c->dev.rx_of));
+    const uint32_t n_sp = m->n_species, n_rx = m->n_reactions, n_comp = m->n_compartments;
+
+    // geometry
+    const abm_compartment* cm = m->compartments;
+    if (cm[0].parent != -1) return bad("compartment 0 must be the root (parent -1)");
+    if (!(std::isfinite(cm[0].size_um) && cm[0].size_um > 0)) return bad("root size must be positive");
+    int64_t ext;
+    SimDev& g = c->geo;
+    if (cm[0].shape == ABM_CUBE) {
+        ext = llround(cm[0].size_um * 1000.0 / unit);
+        g.root_sphere = 0;
+        g.c0[0] = g.c0[1] = g.c0[2] = (int32_t)(ext / 2);
+        c->volume = (double)ext * ext * ext;
+    } else if (cm[0].shape == ABM_SPHERE) {
+        const int64_t r = llround(cm[0].size_um * 1000.0 / unit / 2.0);
+        ext = 2 * r;
+        g.root_sphere = 1;
+        g.root_r2 = r * r;
+        g.c0[0] = g.c0[1] = g.c0[2] = (int32_t)r;
+        c->volume = 4.0 / 3.0 * M_PI * (double)r * r * r;
+    } else {
+        return bad("unknown root shape");
+    }
+    if (ext < 2 || ext >= (1ll << 30)) return bad("root extent must be in [2, 2^30) units");
+    g.ext = (int32_t)ext;
+    g.n_comp = (int32_t)n_comp;
+    for (uint32_t k = 1; k < n_comp; k++) {
+        if (cm[k].parent != 0 || cm[k].shape != ABM_SPHERE) return bad("compartments 1..3 must be spheres in the root");
+        if (!(std::isfinite(cm[k].size_um) && cm[k].size_um > 0)) return bad("compartment size must be positive");
+        const int64_t r = llround(cm[k].size_um * 1000.0 / unit / 2.0);
+        if (r < 1) return bad("child sphere too small");
+        int64_t cc[3];
+        for (int d = 0; d < 3; d++) {
+            if (!std::isfinite(cm[k].center_um[d])) return bad("bad compartment centre");
+            cc[d] = g.c0[d] + llround(cm[k].center_um[d] * 1000.0 / unit);
+            g.cc[k][d] = (int32_t)cc[d];
+        }
+        g.cr2[k] = r * r;
+        if (g.root_sphere) {
+            const int64_t room = ext / 2 - r;
+            int64_t d2 = 0;
+            for (int d = 0; d < 3; d++) d2 += (cc[d] - g.c0[d]) * (cc[d] - g.c0[d]);
+            if (room < 0 || d2 > room * room) return bad("child sphere leaves the root");
+        } else {
+            for (int d = 0; d < 3; d++)
+                if (cc[d] - r < 0 || cc[d] + r > ext) return bad("child sphere leaves the root");
+        }
+        for (uint32_t j = 1; j < k; j++) {
+            const int64_t rj = (int64_t)llround(std::sqrt((double)g.cr2[j]));
+            int64_t d2 = 0;
+            for (int d = 0; d < 3; d++) d2 += (cc[d] - g.cc[j][d]) * (int64_t)(cc[d] - g.cc[j][d]);
+            if (d2 <= (r + rj) * (r + rj)) return bad("child spheres overlap");
+        }
+    }
+
+    // bound on |Z| for any int16 table, so that one fold always suffices
+    const int zmax = 32768;
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < n_sp; i++) {
+        const abm_species& s = m->species[i];
+        if (!(std::isfinite(s.D_um2_s) && s.D_um2_s >= 0)) return bad("diffusion coefficient must be >= 0");
+        if (!prob_ok(s.p_cross) || !prob_ok(s.p_uni) || !prob_ok(s.p_emit)) return bad("species probability outside [0,1]");
+        if (s.compartment < 0 || s.compartment >= (int32_t)n_comp) return bad("species compartment out of range");
+        if (s.uni_to < -1 || s.uni_to >= (int32_t)n_sp) return bad("uni_to names an unknown species");
+        if (s.emit_species < -1 || s.emit_species >= (int32_t)n_sp) return bad("emit_species names an unknown species");
+        SpeciesDev& d = c->dev.sp[i];
+        const double sigma_delta = std::sqrt(2.0 * s.D_um2_s * dt) * 1000.0 / unit;
+        const long long M = llround(sigma_delta * 1048576.0);
+        if (M < 0 || M >= (1ll << 32)) return bad("diffusion step too large for the time step");
+        if ((((uint64_t)zmax * (uint64_t)M + 0x80000000ull) >> 32) > (uint64_t)ext)
+            return bad("diffusion step exceeds the domain");
+        d.M = (uint32_t)M;
+        d.thr_uni = threshold(s.p_uni);
+        d.thr_emit = s.emit_species >= 0 ? threshold(s.p_emit) : 0;
+        d.thr_cross = threshold(s.p_cross);
+        d.uni_to = (int16_t)s.uni_to;
+        d.emit = (int16_t)s.emit_species;
+        d.has_event = (d.thr_uni || d.thr_emit) ? 1u : 0u;
+        d.init_comp = (uint32_t)s.compartment;
+        total += s.initial_count;
+        c->species_end[i] = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFFFull);
+    }
+    if (total >= 0xFFFFFFF0ull) return bad("too many agents for 32-bit ids");
+    c->n0 = total;
+    for (uint32_t r = 0; r < n_rx; r++) {
+        const abm_reaction& q = m->reactions[r];
+        if (q.a < 0 || q.a >= (int32_t)n_sp || q.b < 0 || q.b >= (int32_t)n_sp) return bad("reaction names an unknown species");
+        if (q.a == q.b) return bad("A + A reactions are not supported");
+        if (q.kind != ABM_CONVERT && q.kind != ABM_BIND) return bad("unknown reaction kind");
+        if (q.prod_a < -1 || q.prod_a >= (int32_t)n_sp || q.prod_b < -1 || q.prod_b >= (int32_t)n_sp)
+            return bad("reaction product names an unknown species");
+        if (!prob_ok(q.p_bind) || !prob_ok(q.p_release)) return bad("reaction probability outside [0,1]");
+        if (!std::isfinite(q.radius_nm)) return bad("reaction radius must be finite");
+        if (c->dev.rx_of[q.a][q.b] != 0xFF || c->dev.rx_of[q.b][q.a] != 0xFF)
+            return bad("two reactions for the same species pair");
+        const long long R = llround(q.radius_nm / unit);
+        if (R < 1 || R > 30000) return bad("reaction radius must be in [1, 30000] units");
+        ReactionDev& d = c->dev.rx[r];
+        d.thr_bind = threshold(q.p_bind);
+        d.thr_rel = threshold(q.p_release);
+        d.R = (int32_t)R;
+        d.R2 = (uint32_t)(R * R);
+        d.prod_a = (int16_t)q.prod_a;
+        d.prod_b = (int16_t)q.prod_b;
+        d.kind = (uint8_t)q.kind;
+        d.carrier_a = !(m->species[q.b].D_um2_s < m->species[q.a].D_um2_s);
+        d.a = (uint8_t)q.a;
+        d.b = (uint8_t)q.b;
+        c->dev.rx_of[q.a][q.b] = (uint8_t)r;
+        c->dev.sp[q.a].partner_mask |= 1ull << q.b;
+        c->Rmax = std::max<int64_t>(c->Rmax, R);
+    }
+    c->dev.n_sp = n_sp;
+    c->dev.n_rx = n_rx;
+    c->dev.n_comp = n_comp;
+    c->dev.n_counts = n_sp * n_comp + n_rx + 1;
+    return ABM_OK;
+}
+
+// Grid cell edge 2^shift: about one agent per cell at the initial density,
+// never below the largest contact radius.
+uint32_t auto_shift(const Compiled& c) {
+    const double n = std::max<double>(1.0, (double)c.n0);
+    const double h = std::cbrt(c.volume / n);
+    int s = (int)std::floor(std::log2(std::max(h, 1.0)) + 0.5);
+    int smin = 0;
+    while ((1ll << smin) < c.Rmax) smin++;
+    // at most 1024 cells per axis
+    while ((c.geo.ext >> s) + 1 > 1024) s++;
+    return (uint32_t)std::max(s, smin);
+}
+
+uint64_t cells_for(const Compiled& c, uint32_t shift) {
+    const uint64_t gx = (uint64_t)(c.geo.ext >> shift) + 1;
+    return gx * gx * gx;
+}
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t off[32];
+    size_t total;
+};
+
+// Sub-buffer sizes of a batch arena, in the order carved by carve().
+Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
+    const uint64_t E = C / 2 + 1;
+    const uint64_t Kpad = (K + kTile - 1) / kTile * kTile;
+    const uint64_t tiles = Kpad / kTile + 1;
+    const size_t sizes[] = {
+        16 * C, 16 * C,                        // pm[2]
+        4 * C, 4 * C, 4 * C, 4 * C,            // aid[2], apar[2]
+        8 * C, 8 * C, 4 * C,                   // kr, acc, tgt
+        16 * E, 4 * E, 8 * E,                  // extras
+        16 * (size_t)Bc, 4 * (size_t)Bc,       // births
+        4 * Kpad, 4 * (Kpad + 8),              // cnt, start
+        8 * tiles,                             // scan descriptors
+        sizeof(SimDev) * S, sizeof(ModelDev) * S,
+        8 * (size_t)S * 512, 8 * (size_t)S,    // counts, digests
+        2 * 65536,                             // Gaussian table
+        sizeof(Ctl),
+        4 * kMaxSpecies,                       // staging for admissions
+    };
+    Layout L{};
+    size_t o = 0;
+    const int n = (int)(sizeof(sizes) / sizeof(sizes[0]));
+    for (int i = 0; i < n; i++) {
+        L.off[i] = o;
+        o += align_up(sizes[i]);
+    }
+    L.off[n] = o;
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+struct abm_batch {
+    uint64_t cap_agents = 0, cap_cells = 0;
+    uint32_t max_sims = 0, cap_births = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    bool own_arena = false;
+    Buffers B{};
+    Launch L{};
+    uint32_t* staging = nullptr;
+    cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+    struct HostSim {
+        int state = 0;  // 0 free, 1 active, 2 draining (removed, not yet stepped)
+        uint32_t model_slot = 0;
+        uint64_t n_cells = 0;
+        uint32_t n_counts = 0;
+        uint32_t shift = 0;
+    };
+    std::vector<HostSim> sims;
+    std::vector<uint32_t> cell_off_host;  // persistent sources of async copies
+    uint32_t n_cells_host = 0;
+    std::vector<ModelDev> model_host;   // copies of the uploaded model tables
+    std::vector<int> model_refs;
+    uint32_t n_sims_used = 0;
+    bool failed = false;
+    std::string err;
+};
+
+struct abm_sim {
+    abm_batch* b = nullptr;
+    int32_t id = -1;
+};
+
+namespace {
+
+abm_status fail(abm_batch* b, abm_status st, const std::string& msg) {
+    b->failed = true;
+    b->err = msg;
+    return st;
+}
+
+abm_status cuda_fail(abm_batch* b, cudaError_t e, const char* where) {
+    return fail(b, ABM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(b, e_, #call); \
+    } while (0)
+
+abm_status check_device(std::string* msg) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        *msg = "no CUDA device";
+        return ABM_EDEVICE;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+        *msg = "cannot query the CUDA device";
+        return ABM_EDEVICE;
+    }
+    if (p.major != 10 || p.minor != 3) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "device is sm_%d%d; this library is built for sm_103a", p.major, p.minor);
+        *msg = buf;
+        return ABM_EDEVICE;
+    }
+    return ABM_OK;
+}
+
+// Map the sticky device error word to a status.
+abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
+    if (b->failed) return ABM_ESTATE;
+    Ctl h;
+    CU(cudaMemcpyAsync(&h, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    if (out_ctl) *out_ctl = h;
+    if (h.err == ERR_NONE) return ABM_OK;
+    char buf[160];
+    abm_status st = ABM_ECAPACITY;
+    const char* what = "capacity exceeded";
+    switch (h.err) {
+        case ERR_CAPACITY_AGENTS: what = "agent capacity exceeded"; break;
+        case ERR_CAPACITY_EXTRAS: what = "release buffer capacity exceeded"; break;
+        case ERR_CAPACITY_BIRTHS: what = "births per step exceed the limit"; break;
+        case ERR_TIMEOUT_SCAN: what = "scan look-back wait timed out"; st = ABM_ETIMEOUT; break;
+        case ERR_PLACEMENT: what = "could not place an agent in its compartment"; st = ABM_EINVAL; break;
+        case ERR_ID_SPACE: what = "agent id space exhausted"; break;
+        default: what = "device error"; st = ABM_ECUDA; break;
+    }
+    std::snprintf(buf, sizeof buf, "%s (code %u, info %u)", what, h.err, h.err_info);
+    return fail(b, st, buf);
+}
+
+abm_status capture(abm_batch* b) {
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; k++) {
+        const int steps = k == 0 ? 1 : 8;
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return cuda_fail(b, e, "cudaStreamBeginCapture");
+        }
+        for (int s = 0; s < steps; s++) launch_step(b->B, b->L, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return cuda_fail(b, e, "cudaStreamEndCapture");
+        }
+        e = cudaGraphInstantiate(k == 0 ? &b->g1 : &b->g8, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return cuda_fail(b, e, "cudaGraphInstantiate");
+        }
+    }
+    cudaStreamDestroy(cs);
+    return ABM_OK;
+}
+
+// Re-pack every active simulation's cell range (keys are recomputed from
+// positions every step, so offsets may change between steps).
+abm_status repack_cells(abm_batch* b) {
+    uint64_t off = 0;
+    for (uint32_t s = 0; s < b->n_sims_used; s++) {
+        auto& h = b->sims[s];
+        if (h.state != 1) continue;
+        b->cell_off_host[s] = (uint32_t)off;
+        CU(cudaMemcpyAsync(&b->B.sims[s].cell_off, &b->cell_off_host[s], 4, cudaMemcpyHostToDevice, b->stream));
+        off += h.n_cells;
+    }
+    b->n_cells_host = (uint32_t)off;
+    CU(cudaMemcpyAsync(&b->B.ctl->n_cells, &b->n_cells_host, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return ABM_OK;
+}
+
+uint64_t cells_in_use(const abm_batch* b) {
+    uint64_t off = 0;
+    for (uint32_t s = 0; s < b->n_sims_used; s++)
+        if (b->sims[s].state == 1) off += b->sims[s].n_cells;
+    return off;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+extern "C" {
+
+const char* abm_version(void) { return "abm-b300 1.0 (sm_103a)"; }
+
+void abm_ncdf_table(int16_t* out) {
+    if (out) build_table(out);
+}
+
+size_t abm_batch_arena_bytes(const abm_batch_options* o) {
+    if (!o || !o->capacity_agents || !o->capacity_cells || !o->max_sims || o->max_sims > (uint32_t)kMaxSims)
+        return 0;
+    const uint32_t births = o->births_per_step ? o->births_per_step : kMaxBirths;
+    return layout_for(o->capacity_agents, o->capacity_cells, o->max_sims, births).total;
+}
+
+abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
+    if (!out) return ABM_EINVAL;
+    *out = nullptr;
+    if (!o || !o->capacity_agents || !o->capacity_cells || !o->max_sims || o->max_sims > (uint32_t)kMaxSims)
+        return ABM_EINVAL;
+    if (o->capacity_agents >= 0x7FFFFFFFull || o->capacity_cells >= 0xFFFFF000ull) return ABM_EINVAL;
+    const uint32_t births = o->births_per_step ? o->births_per_step : kMaxBirths;
+    if (births > kMaxBirths) return ABM_EINVAL;
+    std::string msg;
+    abm_status st = check_device(&msg);
+    if (st != ABM_OK) return st;
+    abm_batch* b = new (std::nothrow) abm_batch();
+    if (!b) return ABM_ENOMEM;
+    b->cap_agents = o->capacity_agents;
+    b->cap_cells = o->capacity_cells;
+    b->max_sims = o->max_sims;
+    b->cap_births = births;
+    const Layout lay = layout_for(b->cap_agents, b->cap_cells, b->max_sims, births);
+    auto destroy_and = [&](abm_status s) {
+        abm_batch_destroy(b);
+        return s;
+    };
+    if (o->arena) {
+        if (o->arena_bytes < lay.total || ((uintptr_t)o->arena % kAlign)) return destroy_and(ABM_ENOMEM);
+        b->arena = (char*)o->arena;
+        b->arena_bytes = o->arena_bytes;
+    } else {
+        if (cudaMalloc((void**)&b->arena, lay.total) != cudaSuccess) {
+            cudaGetLastError();
+            b->arena = nullptr;
+            return destroy_and(ABM_ENOMEM);
+        }
+        b->own_arena = true;
+        b->arena_bytes = lay.total;
+    }
+    if (o->stream) {
+        b->stream = (cudaStream_t)o->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return destroy_and(ABM_ECUDA);
+        b->own_stream = true;
+    }
+    char* a = b->arena;
+    int k = 0;
+    auto at = [&](void) { return (void*)(a + lay.off[k++]); };
+    Buffers& B = b->B;
+    B.pm[0] = (int4*)at();
+    B.pm[1] = (int4*)at();
+    B.aid[0] = (uint32_t*)at();
+    B.aid[1] = (uint32_t*)at();
+    B.apar[0] = (uint32_t*)at();
+    B.apar[1] = (uint32_t*)at();
+    B.kr = (uint64_t*)at();
+    B.acc = (uint64_t*)at();
+    B.tgt = (uint32_t*)at();
+    B.xpm = (int4*)at();
+    B.xid = (uint32_t*)at();
+    B.xkr = (uint64_t*)at();
+    B.bpm = (int4*)at();
+    B.bpar = (uint32_t*)at();
+    B.cnt = (uint32_t*)at();
+    B.start = (uint32_t*)at();
+    B.tiles = (uint64_t*)at();
+    B.sims = (SimDev*)at();
+    B.models = (ModelDev*)at();
+    B.counts = (uint64_t*)at();
+    B.digests = (uint64_t*)at();
+    int16_t* ztab = (int16_t*)at();
+    B.ztab = ztab;
+    B.ctl = (Ctl*)at();
+    b->staging = (uint32_t*)at();
+    B.cap_agents = b->cap_agents;
+    B.cap_extras = b->cap_agents / 2 + 1;
+    B.cap_cells = b->cap_cells;
+    B.cap_births = births;
+    B.n_tiles_max = (uint32_t)((b->cap_cells + kTile - 1) / kTile);
+    b->sims.resize(b->max_sims);
+    b->cell_off_host.assign(b->max_sims, 0);
+
+    // launch shapes: grid-stride kernels sized to the resident capacity
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (b->cap_agents + 255) / 256;
+    b->L.threads = 256;
+    b->L.blocks_agents = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 6));
+    b->L.blocks_scan = (int)std::max<uint64_t>(1, std::min<uint64_t>(B.n_tiles_max, (uint64_t)sms * 4));
+
+    std::vector<int16_t> table(65536);
+    if (o->ncdf_table) std::memcpy(table.data(), o->ncdf_table, 2 * 65536);
+    else build_table(table.data());
+#undef CU
+#define CU(call)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) {                                      \
+            cuda_fail(b, e_, #call);                                  \
+            return destroy_and(ABM_ECUDA);                            \
+        }                                                             \
+    } while (0)
+    CU(prepare_kernels(births));
+    CU(cudaMemsetAsync(b->arena, 0, lay.total, b->stream));
+    CU(cudaMemcpyAsync(ztab, table.data(), 2 * 65536, cudaMemcpyHostToDevice, b->stream));
+    Ctl c{};
+    c.epoch = 1;
+    CU(cudaMemcpyAsync(B.ctl, &c, sizeof c, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+#undef CU
+    if (capture(b) != ABM_OK) {
+        cudaGetLastError();
+        return destroy_and(ABM_ECUDA);
+    }
+    *out = b;
+    return ABM_OK;
+}
+
+#define CU(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(b, e_, #call); \
+    } while (0)
+
+abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, uint32_t cell_log2, int32_t* sim_id) {
+    if (!b || !sim_id) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    *sim_id = -1;
+    Compiled* c = new (std::nothrow) Compiled();
+    if (!c) return ABM_ENOMEM;
+    std::string msg;
+    abm_status st = compile_model(model, c, &msg);
+    if (st != ABM_OK) {
+        b->err = msg;  // invalid input does not fail the batch
+        delete c;
+        return st;
+    }
+    const uint32_t shift = cell_log2 ? cell_log2 : auto_shift(*c);
+    if (shift > 30 || (1ll << shift) < c->Rmax) {
+        b->err = "grid cell smaller than a reaction radius";
+        delete c;
+        return ABM_EINVAL;
+    }
+    const uint64_t ncell = cells_for(*c, shift);
+    // slot: a free one (draining slots become free after the next step)
+    int32_t slot = -1;
+    for (uint32_t s = 0; s < b->max_sims; s++)
+        if (b->sims[s].state == 0) {
+            slot = (int32_t)s;
+            break;
+        }
+    if (slot < 0 || cells_in_use(b) + ncell > b->cap_cells) {
+        b->err = slot < 0 ? "no free simulation slot" : "grid cells exhausted";
+        delete c;
+        return ABM_ECAPACITY;
+    }
+    Ctl h;
+    st = sync_and_check(b, &h);
+    if (st != ABM_OK) {
+        delete c;
+        return st;
+    }
+    if ((uint64_t)h.n_in + c->n0 > b->cap_agents) {
+        b->err = "agent capacity exhausted";
+        delete c;
+        return ABM_ECAPACITY;
+    }
+    // model table: reuse an identical upload
+    int mslot = -1;
+    for (size_t m = 0; m < b->model_host.size(); m++)
+        if (b->model_refs[m] > 0 && std::memcmp(&b->model_host[m], &c->dev, sizeof(ModelDev)) == 0) {
+            mslot = (int)m;
+            break;
+        }
+    if (mslot < 0) {
+        for (size_t m = 0; m < b->model_host.size(); m++)
+            if (b->model_refs[m] == 0) {
+                mslot = (int)m;
+                break;
+            }
+        if (mslot < 0) {
+            mslot = (int)b->model_host.size();
+            b->model_host.emplace_back();
+            b->model_refs.push_back(0);
+        }
+        b->model_host[mslot] = c->dev;
+        CU(cudaMemcpyAsync(&b->B.models[mslot], &c->dev, sizeof(ModelDev), cudaMemcpyHostToDevice, b->stream));
+    }
+    b->model_refs[mslot]++;
+    SimDev sd = c->geo;
+    sd.active = 1;
+    sd.model = (uint32_t)mslot;
+    sd.key0 = (uint32_t)seed;
+    sd.key1 = (uint32_t)(seed >> 32);
+    sd.step = 0;
+    sd.next_id = (uint32_t)c->n0;
+    sd.shift = shift;
+    sd.g = (uint32_t)((c->geo.ext >> shift) + 1);
+    sd.n_counts = c->dev.n_counts;
+    sd.counts_off = (uint32_t)slot * 512u;
+    auto& hs = b->sims[slot];
+    hs.state = 1;
+    hs.model_slot = (uint32_t)mslot;
+    hs.n_cells = ncell;
+    hs.n_counts = c->dev.n_counts;
+    hs.shift = shift;
+    b->n_sims_used = std::max<uint32_t>(b->n_sims_used, (uint32_t)slot + 1);
+    CU(cudaMemcpyAsync(&b->B.sims[slot], &sd, sizeof sd, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemcpyAsync(b->staging, c->species_end, 4 * kMaxSpecies, cudaMemcpyHostToDevice, b->stream));
+    const uint32_t nsu = b->n_sims_used;
+    CU(cudaMemcpyAsync(&b->B.ctl->n_sims, &nsu, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(launch_init(b->B, b->L, b->stream, (uint32_t)slot, h.n_in, (uint32_t)c->n0, b->staging, c->dev.n_sp));
+    const uint32_t n_in = h.n_in + (uint32_t)c->n0;
+    CU(cudaMemcpyAsync(&b->B.ctl->n_in, &n_in, 4, cudaMemcpyHostToDevice, b->stream));
+    st = repack_cells(b);  // synchronises (host temporaries above stay alive until then)
+    delete c;
+    if (st != ABM_OK) return st;
+    st = sync_and_check(b);
+    if (st != ABM_OK) return st;
+    *sim_id = slot;
+    return ABM_OK;
+}
+
+abm_status abm_batch_remove(abm_batch* b, int32_t sim) {
+    if (!b) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    const uint32_t zero = 0;
+    CU(cudaMemcpyAsync(&b->B.sims[sim].active, &zero, 4, cudaMemcpyHostToDevice, b->stream));
+    b->sims[sim].state = 2;
+    b->model_refs[b->sims[sim].model_slot]--;
+    return repack_cells(b);
+}
+
+abm_status abm_batch_step(abm_batch* b, uint32_t n) {
+    if (!b) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (n > 0)
+        for (auto& h : b->sims)
+            if (h.state == 2) h.state = 0;  // their agents are dropped by this step
+    while (n >= 8) {
+        CU(cudaGraphLaunch(b->g8, b->stream));
+        n -= 8;
+    }
+    while (n--) CU(cudaGraphLaunch(b->g1, b->stream));
+    return ABM_OK;
+}
+
+abm_status abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, uint32_t n_kernels) {
+    if (!b || !kernel_ms || n_kernels < (uint32_t)kStepKernels) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (n > 0)
+        for (auto& h : b->sims)
+            if (h.state == 2) h.state = 0;
+    cudaEvent_t ev[kStepKernels + 1];
+    for (int k = 0; k <= kStepKernels; k++) CU(cudaEventCreate(&ev[k]));
+    double acc[kStepKernels] = {};
+    cudaError_t e = cudaSuccess;
+    for (uint32_t s = 0; s < n && e == cudaSuccess; s++) {
+        e = launch_step_timed(b->B, b->L, b->stream, ev);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[kStepKernels]);
+        for (int k = 0; k < kStepKernels && e == cudaSuccess; k++) {
+            float ms = 0;
+            e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            acc[k] += ms;
+        }
+    }
+    for (int k = 0; k <= kStepKernels; k++) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return cuda_fail(b, e, "profile step");
+    for (int k = 0; k < kStepKernels; k++) kernel_ms[k] = (float)acc[k];
+    return sync_and_check(b);
+}
+
+abm_status abm_batch_sync(abm_batch* b) {
+    if (!b) return ABM_EINVAL;
+    return sync_and_check(b);
+}
+
+abm_status abm_batch_live_agents(abm_batch* b, uint64_t* out) {
+    if (!b || !out) return ABM_EINVAL;
+    Ctl h;
+    abm_status st = sync_and_check(b, &h);
+    if (st == ABM_OK) *out = h.n_in;
+    return st;
+}
+
+static abm_status observe(abm_batch* b, int32_t sim, int want_digest) {
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    CU(cudaMemsetAsync(b->B.counts + (size_t)sim * 512, 0, 8 * 512, b->stream));
+    if (want_digest) CU(cudaMemsetAsync(b->B.digests + sim, 0, 8, b->stream));
+    CU(launch_observe(b->B, b->L, b->stream, sim, want_digest));
+    return ABM_OK;
+}
+
+abm_status abm_batch_counts(abm_batch* b, int32_t sim, uint64_t* out, size_t cap, size_t* n_out) {
+    if (!b) return ABM_EINVAL;
+    abm_status st = observe(b, sim, 0);
+    if (st != ABM_OK) return st;
+    const size_t n = b->sims[sim].n_counts;
+    if (n_out) *n_out = n;
+    if (out && cap) CU(cudaMemcpyAsync(out, b->B.counts + (size_t)sim * 512, 8 * std::min(cap, n),
+                                       cudaMemcpyDeviceToHost, b->stream));
+    st = sync_and_check(b);
+    if (st == ABM_OK && out && cap < n) return ABM_EINVAL;
+    return st;
+}
+
+abm_status abm_batch_digest(abm_batch* b, int32_t sim, uint64_t* out) {
+    if (!b || !out) return ABM_EINVAL;
+    abm_status st = observe(b, sim, 1);
+    if (st != ABM_OK) return st;
+    CU(cudaMemcpyAsync(out, b->B.digests + sim, 8, cudaMemcpyDeviceToHost, b->stream));
+    return sync_and_check(b);
+}
+
+abm_status abm_batch_dump(abm_batch* b, int32_t sim, abm_record* out, size_t cap, size_t* n_out) {
+    if (!b) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    Ctl h;
+    abm_status st = sync_and_check(b, &h);
+    if (st != ABM_OK) return st;
+    const uint32_t dcap = (uint32_t)std::min<uint64_t>(2ull * h.n_in + 1, 0xFFFFFFF0ull);
+    void* d = nullptr;
+    CU(cudaMalloc(&d, (size_t)dcap * 24));
+    const uint32_t zero = 0;
+    cudaError_t e = cudaMemcpyAsync(&b->B.ctl->dump_n, &zero, 4, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = launch_dump(b->B, b->L, b->stream, sim, d, dcap);
+    uint32_t n = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, &b->B.ctl->dump_n, 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    std::vector<uint4> lo;
+    std::vector<uint2> hi;
+    if (e == cudaSuccess) {
+        lo.resize(n);
+        hi.resize(n);
+        e = cudaMemcpy(lo.data(), d, (size_t)n * 16, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(hi.data(), (char*)d + (size_t)dcap * 16, (size_t)n * 8, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(b, e, "dump");
+    if (n_out) *n_out = n;
+    if (!out) return ABM_OK;
+    if (cap < n) return ABM_EINVAL;
+    std::vector<abm_record> recs(n);
+    for (uint32_t i = 0; i < n; i++) {
+        abm_record& r = recs[i];
+        r.id = lo[i].x;
+        r.species = (uint8_t)(lo[i].y & 0xFF);
+        r.compartment = (uint8_t)((lo[i].y >> 8) & 0xFF);
+        r.flags = (uint8_t)((lo[i].y >> 16) & 0xFF);
+        r.reaction = (uint8_t)(lo[i].y >> 24);
+        r.x = (int32_t)lo[i].z;
+        r.y = (int32_t)lo[i].w;
+        r.z = (int32_t)hi[i].x;
+        r.partner = hi[i].y;
+    }
+    std::sort(recs.begin(), recs.end(), [](const abm_record& p, const abm_record& q) { return p.id < q.id; });
+    std::memcpy(out, recs.data(), (size_t)n * sizeof(abm_record));
+    return ABM_OK;
+}
+
+const char* abm_batch_last_error(const abm_batch* b) { return b ? b->err.c_str() : "null handle"; }
+
+void abm_batch_destroy(abm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->g8) cudaGraphExecDestroy(b->g8);
+    if (b->own_arena && b->arena) cudaFree(b->arena);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// ---------------- single simulation = a batch of one ----------------
+size_t abm_arena_bytes(const abm_model* model, const abm_options* opt) {
+    Compiled* c = new (std::nothrow) Compiled();
+    if (!c) return 0;
+    std::string msg;
+    size_t bytes = 0;
+    if (compile_model(model, c, &msg) == ABM_OK) {
+        const uint32_t shift = opt && opt->cell_log2 ? opt->cell_log2 : auto_shift(*c);
+        const uint64_t cap = opt && opt->capacity_agents ? opt->capacity_agents : c->n0 + c->n0 / 4 + 65536;
+        abm_batch_options o{};
+        o.capacity_agents = cap;
+        o.capacity_cells = cells_for(*c, shift);
+        o.max_sims = 1;
+        o.births_per_step = opt ? opt->births_per_step : 0;
+        bytes = abm_batch_arena_bytes(&o);
+    }
+    delete c;
+    return bytes;
+}
+
+abm_status abm_create(const abm_model* model, uint64_t seed, const abm_options* opt, abm_sim** out) {
+    if (!out) return ABM_EINVAL;
+    *out = nullptr;
+    Compiled* c = new (std::nothrow) Compiled();
+    if (!c) return ABM_ENOMEM;
+    std::string msg;
+    abm_status st = compile_model(model, c, &msg);
+    const uint32_t shift = st == ABM_OK ? (opt && opt->cell_log2 ? opt->cell_log2 : auto_shift(*c)) : 0;
+    const uint64_t n0 = c->n0;
+    const uint64_t cells = st == ABM_OK ? cells_for(*c, shift) : 0;
+    const bool small_cell = st == ABM_OK && (1ll << shift) < c->Rmax;
+    delete c;
+    if (st != ABM_OK || small_cell || shift > 30) return ABM_EINVAL;
+    abm_batch_options o{};
+    o.capacity_agents = opt && opt->capacity_agents ? opt->capacity_agents : n0 + n0 / 4 + 65536;
+    if (o.capacity_agents < n0) return ABM_ECAPACITY;
+    o.capacity_cells = cells;
+    o.max_sims = 1;
+    o.births_per_step = opt ? opt->births_per_step : 0;
+    o.arena = opt ? opt->arena : nullptr;
+    o.arena_bytes = opt ? opt->arena_bytes : 0;
+    o.stream = opt ? opt->stream : nullptr;
+    o.ncdf_table = opt ? opt->ncdf_table : nullptr;
+    abm_batch* b = nullptr;
+    st = abm_batch_create(&o, &b);
+    if (st != ABM_OK) return st;
+    int32_t id = -1;
+    st = abm_batch_add(b, model, seed, shift, &id);
+    if (st != ABM_OK) {
+        abm_batch_destroy(b);
+        return st;
+    }
+    abm_sim* s = new (std::nothrow) abm_sim();
+    if (!s) {
+        abm_batch_destroy(b);
+        return ABM_ENOMEM;
+    }
+    s->b = b;
+    s->id = id;
+    *out = s;
+    return ABM_OK;
+}
+
+abm_status abm_step(abm_sim* s, uint32_t n) { return s ? abm_batch_step(s->b, n) : ABM_EINVAL; }
+abm_status abm_counts(abm_sim* s, uint64_t* out, size_t cap, size_t* n_out) {
+    return s ? abm_batch_counts(s->b, s->id, out, cap, n_out) : ABM_EINVAL;
+}
+abm_status abm_digest(abm_sim* s, uint64_t* out) { return s ? abm_batch_digest(s->b, s->id, out) : ABM_EINVAL; }
+abm_status abm_dump(abm_sim* s, abm_record* out, size_t cap, size_t* n_out) {
+    return s ? abm_batch_dump(s->b, s->id, out, cap, n_out) : ABM_EINVAL;
+}
+abm_status abm_sync(abm_sim* s) { return s ? abm_batch_sync(s->b) : ABM_EINVAL; }
+abm_status abm_profile_step(abm_sim* s, uint32_t n, float* kernel_ms, uint32_t n_kernels) {
+    return s ? abm_batch_profile_step(s->b, n, kernel_ms, n_kernels) : ABM_EINVAL;
+}
+const char* abm_kernel_name(uint32_t k) {
+    static const char* names[] = {"k_move", "k_scan", "k_scatter", "k_propose", "k_accept", "k_finalize"};
+    return k < (uint32_t)kStepKernels ? names[k] : nullptr;
+}
+abm_status abm_step_index(abm_sim* s, uint32_t* out) {
+    if (!s || !out) return ABM_EINVAL;
+    abm_batch* b = s->b;
+    abm_status st = sync_and_check(b);
+    if (st != ABM_OK) return st;
+    CU(cudaMemcpy(out, &b->B.sims[s->id].step, 4, cudaMemcpyDeviceToHost));
+    return ABM_OK;
+}
+const char* abm_last_error(const abm_sim* s) { return s ? abm_batch_last_error(s->b) : "null handle"; }
+void abm_destroy(abm_sim* s) {
+    if (!s) return;
+    abm_batch_destroy(s->b);
+    delete s;
+}
+
+abm_status abm_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n) {
+    if (!ctr || !key || !out) return ABM_EINVAL;
+    std::string msg;
+    if (check_device(&msg) != ABM_OK) return ABM_EDEVICE;
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dc, 16 * n + 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dk, 8 * n + 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dout, 16 * n + 16);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, 16 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, key, 8 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_debug_philox(dc, dk, dout, n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 16 * n, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dk);
+    cudaFree(dout);
+    return e == cudaSuccess ? ABM_OK : ABM_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// engine.cuh — device-side data layout and helpers of the step engine.
+//
+// Layout in HBM (one arena per batch, 256-byte aligned sub-buffers):
+//   pm[2][C]     int4 {x, y, z, meta}   agent record, double-buffered
+//   aid[2][C]    u32 agent id           (ids are per simulation)
+//   apar[2][C]   u32 partner id         (valid for carriers only)
+//   kr[C]        u64 (cell << 32 | rank within cell) from the move pass
+//   acc[C]       u64 proposal slot, min of (dist^2 << 32 | proposer id)
+//   tgt[C]       u32 index of the agent each proposer chose
+//   xpm/xid/xkr  released partners appended by the move pass (C/2 + 1)
+//   bpm/bpar     births of the step (B)
+//   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
+//   tiles[]      decoupled look-back descriptors of the scan
+//   sims[S], models[S], obs (counts/digests), ctl
+//
+// meta word: bits 0-5 species, 6-7 compartment, 8 carrier, 9 carrier is
+// reactant a, 10 dead, 11 absorbed (became hidden this step), 12-19 reaction
+// of the complex, 20-31 simulation slot.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace abm {
+
+constexpr int kMaxSpecies = 64;
+constexpr int kMaxReactions = 255;
+constexpr int kMaxComp = 4;
+constexpr int kMaxSims = 4096;
+constexpr uint32_t kMaxBirths = 8192;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint64_t kEmpty = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint64_t kInvalidKey = 0xFFFFFFFFFFFFFFFFull;
+
+constexpr uint32_t M_SP = 0x3Fu;
+constexpr uint32_t M_COMP_SHIFT = 6, M_COMP = 0xC0u;
+constexpr uint32_t M_BOUND = 1u << 8;
+constexpr uint32_t M_ROLE_A = 1u << 9;
+constexpr uint32_t M_DEAD = 1u << 10;
+constexpr uint32_t M_ABSORBED = 1u << 11;
+constexpr uint32_t M_RXN_SHIFT = 12, M_RXN = 0xFFu << 12;
+constexpr uint32_t M_SIM_SHIFT = 20;
+
+// device error codes (ctl.err); mapped to abm_status on the host
+enum : uint32_t {
+    ERR_NONE = 0,
+    ERR_CAPACITY_AGENTS = 1,
+    ERR_CAPACITY_EXTRAS = 2,
+    ERR_CAPACITY_BIRTHS = 3,
+    ERR_TIMEOUT_SCAN = 4,
+    ERR_PLACEMENT = 5,
+    ERR_ID_SPACE = 6,
+    ERR_CAPACITY_DUMP = 7,
+};
+
+struct SpeciesDev {          // 48 bytes
+    uint64_t thr_uni, thr_emit, thr_cross;
+    uint64_t partner_mask;   // bit b: a reaction (this species, b) exists
+    uint32_t M;              // Gaussian multiplier, 0 = immobile
+    int16_t uni_to, emit;    // -1 = death / none
+    uint32_t has_event;      // thr_uni or thr_emit nonzero
+    uint32_t init_comp;      // compartment of the initial agents
+};
+
+struct ReactionDev {         // 32 bytes
+    uint64_t thr_bind, thr_rel;
+    uint32_t R2;
+    int32_t R;
+    int16_t prod_a, prod_b;
+    uint8_t kind, carrier_a, a, b;
+};
+
+struct ModelDev {
+    SpeciesDev sp[kMaxSpecies];
+    ReactionDev rx[kMaxReactions + 1];
+    uint8_t rx_of[kMaxSpecies][kMaxSpecies];  // 0xFF = none
+    uint32_t n_sp, n_rx, n_comp, n_counts;
+};
+
+struct SimDev {              // per simulation slot
+    uint32_t active;         // 1 while stepping
+    uint32_t model;
+    uint32_t key0, key1;     // Philox key = seed
+    uint32_t step;           // local step t
+    uint32_t next_id;
+    int32_t ext;             // positions in [0, ext]
+    int32_t root_sphere;
+    int64_t root_r2;
+    int32_t c0[3];
+    int32_t n_comp;
+    int32_t cc[kMaxComp][3]; // child centres (index 1..)
+    int64_t cr2[kMaxComp];   // child radius^2
+    uint32_t shift;          // cell edge 2^shift
+    uint32_t g;              // cells per axis
+    uint32_t cell_off;       // first global cell
+    uint32_t n_counts;       // counts vector length
+    uint32_t counts_off;     // offset into the counts buffer
+    uint32_t pad[3];
+};
+
+struct Ctl {
+    uint32_t n_in;           // agents in the current buffer
+    uint32_t n_extra;        // released partners of this step
+    uint32_t n_sorted;       // agents after the scatter
+    uint32_t n_births;       // births of this step
+    uint32_t cur;            // current buffer
+    uint32_t n_cells;        // cells in use
+    uint32_t scan_ticket;
+    uint32_t epoch;          // global step counter (look-back tags)
+    uint32_t err;
+    uint32_t err_info;
+    uint32_t n_sims;         // sim slots in use (upper bound of the table)
+    uint32_t dump_n;
+    uint32_t pad[4];
+};
+
+struct Buffers {
+    int4* pm[2];
+    uint32_t* aid[2];
+    uint32_t* apar[2];
+    uint64_t* kr;
+    uint64_t* acc;
+    uint32_t* tgt;
+    int4* xpm;
+    uint32_t* xid;
+    uint64_t* xkr;
+    int4* bpm;
+    uint32_t* bpar;
+    uint32_t* cnt;
+    uint32_t* start;
+    uint64_t* tiles;
+    SimDev* sims;
+    ModelDev* models;
+    uint64_t* counts;
+    uint64_t* digests;
+    const int16_t* ztab;
+    Ctl* ctl;
+    uint64_t cap_agents;
+    uint64_t cap_extras;
+    uint64_t cap_cells;
+    uint32_t cap_births;
+    uint32_t n_tiles_max;
+};
+
+// ------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64 multiplies with Weyl-sequence key bumps between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Gaussian step: sign-magnitude, rounded half up, so d(-Z) = -d(Z) exactly.
+__device__ __forceinline__ int32_t gauss_step(int32_t z, uint32_t M) {
+    const uint32_t mag = (uint32_t)(z < 0 ? -z : z);
+    const uint32_t d = (uint32_t)(((uint64_t)mag * M + 0x80000000ull) >> 32);
+    return z < 0 ? -(int32_t)d : (int32_t)d;
+}
+
+// Fold about the half-integer walls -1/2 and ext+1/2 (counting-measure
+// preserving reflection).  |v - x| <= ext guarantees one fold suffices.
+__device__ __forceinline__ int32_t fold(int32_t v, int32_t ext) {
+    if (v < 0) return -v - 1;
+    if (v > ext) return 2 * ext + 1 - v;
+    return v;
+}
+
+__device__ __forceinline__ int64_t d2c(int32_t x, int32_t y, int32_t z, const int32_t* c) {
+    const int64_t dx = x - c[0], dy = y - c[1], dz = z - c[2];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Compartment holding a point; -1 outside a spherical root.
+__device__ __forceinline__ int locate(const SimDev& S, int32_t x, int32_t y, int32_t z) {
+    if (S.root_sphere && d2c(x, y, z, S.c0) > S.root_r2) return -1;
+    for (int k = 1; k < S.n_comp; k++)
+        if (d2c(x, y, z, S.cc[k]) <= S.cr2[k]) return k;
+    return 0;
+}
+
+__device__ __forceinline__ uint32_t cell_of(const SimDev& S, int32_t x, int32_t y, int32_t z) {
+    const uint32_t g = S.g;
+    return S.cell_off + ((uint32_t)(z >> S.shift) * g + (uint32_t)(y >> S.shift)) * g +
+           (uint32_t)(x >> S.shift);
+}
+
+// MurmurHash3 64-bit finaliser (Appleby), for the order-independent digest.
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__device__ __forceinline__ uint64_t record_hash(uint32_t id, uint32_t sp, uint32_t comp, uint32_t flags,
+                                                uint32_t rxn, int32_t x, int32_t y, int32_t z,
+                                                uint32_t partner) {
+    uint64_t h = fmix64((uint64_t)id | (uint64_t)sp << 32 | (uint64_t)comp << 40 |
+                        (uint64_t)flags << 48 | (uint64_t)rxn << 56);
+    h = fmix64(h ^ ((uint64_t)(uint32_t)x | (uint64_t)(uint32_t)y << 32));
+    h = fmix64(h ^ ((uint64_t)(uint32_t)z | (uint64_t)partner << 32));
+    return h;
+}
+
+__device__ __forceinline__ void raise_error(Ctl* ctl, uint32_t code, uint32_t info) {
+    if (atomicCAS(&ctl->err, 0u, code) == 0u) ctl->err_info = info;
+}
+
+// ------------------------------------------------------------------------
+// Host-side launch wrappers (kernels.cu).
+struct Launch {
+    int blocks_agents;       // grid of the per-agent kernels (grid-stride)
+    int threads;             // 256
+    int blocks_scan;
+};
+
+cudaError_t prepare_kernels(uint32_t cap_births);
+cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s);
+cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim,
+                        uint32_t base, uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp);
+cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest);
+// The step with a CUDA event before and after each of its kernels (ev[0..6]).
+constexpr int kStepKernels = 6;
+cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev);
+cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim, void* d_out,
+                        uint32_t cap);
+cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+                                cudaStream_t s);
+
+}  // namespace abm

@@ -1,0 +1,703 @@
+// kernels.cu — the per-step CUDA kernels (sm_103a) of the molecule-agent engine.
+//
+// One step (paper Sec. 2: diffusion, proximity binding, product release,
+// expression, degradation, compartment migration) is six launches over the
+// whole batch of simulations, all reading their sizes from the device
+// control block so that a captured CUDA graph replays them unchanged:
+//
+//   k_move      P1 events + P2 Brownian move + cell key + histogram rank
+//   k_scan      exclusive scan of the cell histogram (decoupled look-back)
+//   k_scatter   reorder every live agent by cell into the other buffer
+//   k_propose   27-cell neighbour query, nearest eligible partner, atomicMin
+//   k_accept    final-edge rule and reaction application
+//   k_finalize  births (ids ranked by parent id), per-step bookkeeping
+//
+// The engine never depends on storage order: every decision is a function
+// of the set of (id, state) pairs, so atomics may run in any order.
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+
+#include "engine.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace abm {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kScanV = 16;
+constexpr int kTile = kThreads * kScanV;  // 4096 cells per scan tile
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// Warp-aggregated slot reservation: one atomicAdd per group of threads that
+// reach this point together.
+__device__ __forceinline__ uint32_t reserve(uint32_t* counter) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    uint32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, g.size());
+    return g.shfl(base, 0) + g.thread_rank();
+}
+
+// P2 for one agent.  p.w carries the compartment bits, updated on crossing.
+__device__ __forceinline__ void brownian_move(const SimDev& S, const SpeciesDev& sd,
+                                              const int16_t* __restrict__ ztab, int4& p,
+                                              uint32_t id, uint32_t t) {
+    const uint32_t M = sd.M;
+    if (M == 0) return;
+    const uint4 m = philox(make_uint4(id, t, 0u, 0u), S.key0, S.key1);
+    int32_t x = p.x + gauss_step(__ldg(&ztab[m.x >> 16]), M);
+    int32_t y = p.y + gauss_step(__ldg(&ztab[m.y >> 16]), M);
+    int32_t z = p.z + gauss_step(__ldg(&ztab[m.z >> 16]), M);
+    if (!S.root_sphere) {
+        x = fold(x, S.ext);
+        y = fold(y, S.ext);
+        z = fold(z, S.ext);
+    }
+    const int c = locate(S, x, y, z);
+    if (c < 0) return;  // would leave the spherical cell: rejected
+    const uint32_t comp = ((uint32_t)p.w & M_COMP) >> M_COMP_SHIFT;
+    if ((uint32_t)c != comp) {
+        if ((uint64_t)m.w >= sd.thr_cross) return;  // membrane: rejected
+        p.w = (int)(((uint32_t)p.w & ~M_COMP) | ((uint32_t)c << M_COMP_SHIFT));
+    }
+    p.x = x;
+    p.y = y;
+    p.z = z;
+}
+
+// ------------------------------------------------------------------------
+// k_move: P1 first-order events and P2 move for every agent of the current
+// buffer, then the cell key and the agent's rank inside its cell (the value
+// returned by the histogram atomic), which the scatter uses directly.
+__global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
+    Ctl* ctl = B.ctl;
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t cur = ctl->cur;
+    const uint32_t n = ctl->n_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->scan_ticket = 0;
+        ctl->n_sorted = 0;  // the scan's last tile writes the real count
+    }
+    int4* __restrict__ pm = B.pm[cur];
+    const uint32_t* __restrict__ aid = B.aid[cur];
+    const uint32_t* __restrict__ apar = B.apar[cur];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int4 p = pm[i];
+        uint32_t meta = (uint32_t)p.w;
+        if (meta & (M_DEAD | M_ABSORBED)) {
+            B.kr[i] = kInvalidKey;
+            continue;
+        }
+        const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+        if (!S.active) {
+            B.kr[i] = kInvalidKey;
+            continue;
+        }
+        const ModelDev& Mo = B.models[S.model];
+        const uint32_t id = aid[i];
+        const uint32_t t = S.step;
+        bool alive = true, emit = false, released = false;
+        int4 q = p;
+        uint32_t qid = 0;
+        if (meta & M_BOUND) {
+            const uint4 e = philox(make_uint4(id, t, 1u, 0u), S.key0, S.key1);
+            const ReactionDev& R = Mo.rx[(meta & M_RXN) >> M_RXN_SHIFT];
+            if ((uint64_t)e.x < R.thr_rel) {
+                const bool ra = meta & M_ROLE_A;
+                const int cprod = ra ? R.prod_a : R.prod_b;
+                const int hprod = ra ? R.prod_b : R.prod_a;
+                meta &= ~(M_BOUND | M_ROLE_A | M_RXN);
+                if (hprod >= 0) {
+                    released = true;
+                    qid = apar[i];
+                    q.w = (int)((meta & ~M_SP) | (uint32_t)hprod);
+                }
+                if (cprod >= 0) meta = (meta & ~M_SP) | (uint32_t)cprod;
+                else alive = false;
+            }
+        } else {
+            const SpeciesDev& sd = Mo.sp[meta & M_SP];
+            if (sd.has_event) {
+                const uint4 e = philox(make_uint4(id, t, 1u, 0u), S.key0, S.key1);
+                if ((uint64_t)e.y < sd.thr_uni) {
+                    if (sd.uni_to >= 0) meta = (meta & ~M_SP) | (uint32_t)sd.uni_to;
+                    else alive = false;
+                } else if ((uint64_t)e.z < sd.thr_emit) {
+                    emit = true;
+                }
+            }
+        }
+        if (alive) {
+            p.w = (int)meta;
+            brownian_move(S, Mo.sp[meta & M_SP], B.ztab, p, id, t);
+            meta = (uint32_t)p.w;  // compartment after the move
+            const uint32_t key = cell_of(S, p.x, p.y, p.z);
+            const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
+            B.kr[i] = (uint64_t)key << 32 | rank;
+            pm[i] = p;
+        } else {
+            B.kr[i] = kInvalidKey;
+        }
+        if (emit) {
+            const uint32_t k = reserve(&ctl->n_births);
+            if (k < B.cap_births) {
+                const uint32_t child = (uint32_t)Mo.sp[meta & M_SP].emit;
+                B.bpm[k] = make_int4(p.x, p.y, p.z,
+                                     (int)((meta & ~(M_SP | M_RXN | M_BOUND | M_ROLE_A)) | child));
+                B.bpar[k] = id;
+            } else {
+                raise_error(ctl, ERR_CAPACITY_BIRTHS, k);
+            }
+        }
+        if (released) {
+            brownian_move(S, Mo.sp[(uint32_t)q.w & M_SP], B.ztab, q, qid, t);
+            const uint32_t k = reserve(&ctl->n_extra);
+            if (k < B.cap_extras) {
+                const uint32_t key = cell_of(S, q.x, q.y, q.z);
+                const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
+                B.xpm[k] = q;
+                B.xid[k] = qid;
+                B.xkr[k] = (uint64_t)key << 32 | rank;
+            } else {
+                raise_error(ctl, ERR_CAPACITY_EXTRAS, k);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_scan: start[c] = sum of cnt[0..c), cnt reset to zero, single pass.
+// Tiles are taken from a ticket counter in launch order, so a tile only
+// waits for tiles whose owners are already running.  Each tile publishes
+// its aggregate, then its inclusive prefix, tagged with the step epoch.
+__global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
+    Ctl* ctl = B.ctl;
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t n = ctl->n_cells;
+    const uint32_t ntiles = (n + kTile - 1) / kTile;
+    const uint64_t epoch = (uint64_t)(ctl->epoch & 0x3FFFFFFFu);
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_warp[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->scan_ticket, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) return;
+        const uint32_t base = tile * kTile + threadIdx.x * kScanV;
+        uint32_t v[kScanV];
+        uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
+#pragma unroll
+        for (int k = 0; k < kScanV / 4; k++) {
+            const uint4 u = src[k];
+            v[4 * k] = u.x;
+            v[4 * k + 1] = u.y;
+            v[4 * k + 2] = u.z;
+            v[4 * k + 3] = u.w;
+            src[k] = make_uint4(0, 0, 0, 0);
+        }
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanV; k++) tsum += v[k];
+        // block exclusive scan of the thread sums
+        uint32_t incl = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t wpre = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; w++) {
+            const uint32_t sw = s_warp[w];
+            if (w < warp) wpre += sw;
+            total += sw;
+        }
+        const uint32_t texcl = wpre + incl - tsum;
+        if (threadIdx.x == 0) {
+            uint64_t* desc = B.tiles + tile;
+            uint32_t excl = 0;
+            if (tile == 0) {
+                st_release(desc, epoch << 34 | 2ull << 32 | total);
+            } else {
+                st_release(desc, epoch << 34 | 1ull << 32 | total);
+                int64_t k = (int64_t)tile - 1;
+                uint32_t spins = 0;
+                while (k >= 0) {
+                    const uint64_t d = ld_acquire(B.tiles + k);
+                    const uint32_t st = (uint32_t)(d >> 32) & 3u;
+                    if ((d >> 34) != epoch || st == 0) {
+                        if (++spins > kSpinLimit) {
+                            raise_error(ctl, ERR_TIMEOUT_SCAN, tile);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    excl += (uint32_t)d;
+                    if (st == 2) break;
+                    k--;
+                }
+                st_release(desc, epoch << 34 | 2ull << 32 | (excl + total));
+            }
+            s_prefix = excl;
+        }
+        __syncthreads();
+        const uint32_t pre = s_prefix + texcl;
+        uint32_t run = pre;
+        uint4* dst = reinterpret_cast<uint4*>(B.start + base);
+#pragma unroll
+        for (int k = 0; k < kScanV / 4; k++) {
+            uint4 o;
+            o.x = run; run += v[4 * k];
+            o.y = run; run += v[4 * k + 1];
+            o.z = run; run += v[4 * k + 2];
+            o.w = run; run += v[4 * k + 3];
+            dst[k] = o;
+        }
+        if (tile == ntiles - 1 && threadIdx.x == 0) {
+            B.start[n] = s_prefix + total;  // cells past n are empty
+            ctl->n_sorted = s_prefix + total;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_scatter: every live agent (and every released partner) to its slot
+// start[cell] + rank in the other buffer; clears its proposal slot.
+__global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
+    Ctl* ctl = B.ctl;
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
+    const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        uint64_t kr;
+        int4 p;
+        uint32_t id, par = kNone;
+        if (j < n_in) {
+            kr = B.kr[j];
+            if (kr == kInvalidKey) continue;
+            p = B.pm[cur][j];
+            id = B.aid[cur][j];
+            if ((uint32_t)p.w & M_BOUND) par = B.apar[cur][j];
+        } else {
+            const uint32_t k = j - n_in;
+            kr = B.xkr[k];
+            p = B.xpm[k];
+            id = B.xid[k];
+        }
+        const uint32_t dest = B.start[kr >> 32] + (uint32_t)kr;
+        if (dest >= B.cap_agents) {
+            raise_error(ctl, ERR_CAPACITY_AGENTS, dest);
+            continue;
+        }
+        B.pm[nxt][dest] = p;
+        B.aid[nxt][dest] = id;
+        if ((uint32_t)p.w & M_BOUND) B.apar[nxt][dest] = par;
+        B.acc[dest] = kEmpty;
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_propose: each free agent of a proposing species looks at the 27 cells
+// around its own (three x-contiguous ranges per (dy, dz) row), keeps the
+// nearest eligible partner by (dist^2, id), and claims it with atomicMin on
+// the partner's slot using the key (dist^2 << 32 | own id).
+__global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
+    Ctl* ctl = B.ctl;
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t nxt = ctl->cur ^ 1u;
+    const uint32_t n = ctl->n_sorted;
+    const int4* __restrict__ pm = B.pm[nxt];
+    const uint32_t* __restrict__ aid = B.aid[nxt];
+    const uint32_t* __restrict__ start = B.start;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 p = pm[i];
+        const uint32_t meta = (uint32_t)p.w;
+        uint32_t target = kNone;
+        if (!(meta & M_BOUND)) {
+            const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+            const ModelDev& Mo = B.models[S.model];
+            const uint32_t sp = meta & M_SP;
+            const uint64_t mask = Mo.sp[sp].partner_mask;
+            if (mask) {
+                const uint32_t ida = aid[i];
+                const uint32_t t = S.step;
+                const int g = (int)S.g;
+                const int sh = (int)S.shift;
+                const int cx = p.x >> sh, cy = p.y >> sh, cz = p.z >> sh;
+                const int x0 = cx > 0 ? cx - 1 : 0;
+                const int x1 = cx < g - 1 ? cx + 1 : g - 1;
+                uint64_t best = kEmpty;
+                for (int zz = cz - 1; zz <= cz + 1; zz++) {
+                    if (zz < 0 || zz >= g) continue;
+                    for (int yy = cy - 1; yy <= cy + 1; yy++) {
+                        if (yy < 0 || yy >= g) continue;
+                        const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
+                        const uint32_t j1 = start[row + x1 + 1];
+                        for (uint32_t j = start[row + x0]; j < j1; j++) {
+                            if (j == i) continue;
+                            const int4 q = pm[j];
+                            const uint32_t mq = (uint32_t)q.w;
+                            if (mq & M_BOUND) continue;
+                            if ((mq ^ meta) & M_COMP) continue;
+                            const uint32_t spb = mq & M_SP;
+                            if (!((mask >> spb) & 1ull)) continue;
+                            const ReactionDev& R = Mo.rx[Mo.rx_of[sp][spb]];
+                            const int dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+                            if (abs(dx) > R.R || abs(dy) > R.R || abs(dz) > R.R) continue;
+                            const uint32_t d2 = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+                            if (d2 > R.R2) continue;
+                            const uint32_t idb = aid[j];
+                            const uint64_t key = (uint64_t)d2 << 32 | idb;
+                            if (key >= best) continue;
+                            const uint32_t lo = min(ida, idb), hi = max(ida, idb);
+                            const uint4 u = philox(make_uint4(lo, hi, t, 1u), S.key0, S.key1);
+                            if ((uint64_t)u.x >= R.thr_bind) continue;
+                            best = key;
+                            target = j;
+                        }
+                    }
+                }
+                if (target != kNone) atomicMin((unsigned long long*)&B.acc[target],
+                                               (unsigned long long)((best & 0xFFFFFFFF00000000ull) | ida));
+            }
+        }
+        B.tgt[i] = target;
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_accept: edge i -> j is final iff j's slot holds i's id and nobody
+// proposed to i.  Final edges are disjoint, so each is applied by its
+// proposer without further synchronisation.
+__global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
+    Ctl* ctl = B.ctl;
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t nxt = ctl->cur ^ 1u;
+    const uint32_t n = ctl->n_sorted;
+    int4* __restrict__ pm = B.pm[nxt];
+    uint32_t* __restrict__ aid = B.aid[nxt];
+    uint32_t* __restrict__ apar = B.apar[nxt];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t j = B.tgt[i];
+        if (j == kNone) continue;
+        const uint64_t kb = B.acc[j];
+        const uint32_t ida = aid[i];
+        if ((uint32_t)kb != ida || B.acc[i] != kEmpty) continue;
+        uint32_t* wa = reinterpret_cast<uint32_t*>(&pm[i]) + 3;
+        uint32_t* wb = reinterpret_cast<uint32_t*>(&pm[j]) + 3;
+        uint32_t ma = *wa, mb = *wb;
+        const SimDev& S = B.sims[ma >> M_SIM_SHIFT];
+        const ModelDev& Mo = B.models[S.model];
+        const uint32_t r = Mo.rx_of[ma & M_SP][mb & M_SP];
+        const ReactionDev& R = Mo.rx[r];
+        if (R.kind == 0) {  // CONVERT
+            ma = R.prod_a >= 0 ? (ma & ~M_SP) | (uint32_t)R.prod_a : ma | M_DEAD;
+            mb = R.prod_b >= 0 ? (mb & ~M_SP) | (uint32_t)R.prod_b : mb | M_DEAD;
+        } else if (R.carrier_a) {  // BIND, a carries b
+            ma |= M_BOUND | M_ROLE_A | (r << M_RXN_SHIFT);
+            apar[i] = aid[j];
+            mb |= M_ABSORBED;
+        } else {  // BIND, b carries a
+            mb |= M_BOUND | (r << M_RXN_SHIFT);
+            apar[j] = ida;
+            ma |= M_ABSORBED;
+        }
+        *wa = ma;
+        *wb = mb;
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_finalize (one block): newborns get ids next_id + rank, the rank ordering
+// births of the same simulation by parent id, and are appended after the
+// sorted agents; then the step's bookkeeping (buffer flip, step counters).
+__global__ void __launch_bounds__(1024) k_finalize(Buffers B) {
+    extern __shared__ uint64_t s_key[];
+    Ctl* ctl = B.ctl;
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t nxt = ctl->cur ^ 1u;
+    const uint32_t ns = ctl->n_sorted;
+    uint32_t nb = ctl->n_births;
+    if (nb > B.cap_births) nb = B.cap_births;  // the overflow was already flagged
+    if (nb && (uint64_t)ns + nb > B.cap_agents) {
+        if (threadIdx.x == 0) raise_error(ctl, ERR_CAPACITY_AGENTS, ns + nb);
+        return;
+    }
+    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x)
+        s_key[k] = (uint64_t)((uint32_t)B.bpm[k].w >> M_SIM_SHIFT) << 32 | B.bpar[k];
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
+        const uint64_t key = s_key[k];
+        uint32_t lt = 0;
+        for (uint32_t j = 0; j < nb; j++) {
+            const uint64_t o = s_key[j];
+            lt += ((o >> 32) == (key >> 32)) & (o < key);
+        }
+        const uint32_t s = (uint32_t)(key >> 32);
+        const uint64_t nid = (uint64_t)B.sims[s].next_id + lt;
+        if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
+        B.pm[nxt][ns + k] = B.bpm[k];
+        B.aid[nxt][ns + k] = (uint32_t)nid;
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
+        const uint64_t key = s_key[k];
+        uint32_t lt = 0, gt = 0;
+        for (uint32_t j = 0; j < nb; j++) {
+            const uint64_t o = s_key[j];
+            const bool same = (o >> 32) == (key >> 32);
+            lt += same & (o < key);
+            gt += same & (o > key);
+        }
+        if (gt == 0) B.sims[key >> 32].next_id += lt + 1;  // one writer per sim
+    }
+    const uint32_t n_sims = ctl->n_sims;
+    for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
+        if (B.sims[s].active) B.sims[s].step += 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->n_in = ns + nb;
+        ctl->n_extra = 0;
+        ctl->n_births = 0;
+        ctl->cur = nxt;
+        ctl->epoch = ctl->epoch + 1;
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_init: initial placement of simulation `sim` (ids 0..n0-1, species-major)
+// by rejection: uniform integer coordinates from Philox(id, attempt, 0, 2)
+// until the point lies in the species' compartment.
+__global__ void __launch_bounds__(kThreads) k_init(Buffers B, uint32_t sim, uint32_t base, uint32_t n0,
+                                                   const uint32_t* __restrict__ species_end, uint32_t n_sp) {
+    Ctl* ctl = B.ctl;
+    const uint32_t cur = ctl->cur;
+    const SimDev& S = B.sims[sim];
+    const ModelDev& Mo = B.models[S.model];
+    const uint64_t span = (uint64_t)S.ext + 1;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n0; k += gridDim.x * blockDim.x) {
+        uint32_t sp = 0;
+        while (sp + 1 < n_sp && species_end[sp] <= k) sp++;
+        const int want = (int)Mo.sp[sp].init_comp;
+        bool placed = false;
+        int32_t x = 0, y = 0, z = 0;
+        for (uint32_t attempt = 0; attempt < (1u << 24) && !placed; attempt++) {
+            const uint4 w = philox(make_uint4(k, attempt, 0u, 2u), S.key0, S.key1);
+            x = (int32_t)(((uint64_t)w.x * span) >> 32);
+            y = (int32_t)(((uint64_t)w.y * span) >> 32);
+            z = (int32_t)(((uint64_t)w.z * span) >> 32);
+            placed = locate(S, x, y, z) == want;
+        }
+        if (!placed) raise_error(ctl, ERR_PLACEMENT, k);
+        B.pm[cur][base + k] = make_int4(x, y, z, (int)((sim << M_SIM_SHIFT) | ((uint32_t)want << M_COMP_SHIFT) | sp));
+        B.aid[cur][base + k] = k;
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_observe: per-simulation counts (free by species and compartment, bound
+// complexes by reaction) and, optionally, the order-independent digest
+// (wrapping sum of a hash of every agent record, hidden partners included).
+// Each block owns one contiguous range of the cell-sorted array, so almost
+// all of its agents belong to one simulation: those are counted in a
+// shared-memory histogram and flushed with one atomic per bin.
+__global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_sim, int want_digest) {
+    __shared__ uint32_t sh[512];
+    __shared__ uint32_t s_sim;
+    Ctl* ctl = B.ctl;
+    const uint32_t cur = ctl->cur;
+    const uint32_t n = ctl->n_in;
+    const uint32_t chunk = ((n + gridDim.x - 1) / gridDim.x + kThreads - 1) / kThreads * kThreads;
+    const uint32_t begin = blockIdx.x * chunk;
+    const uint32_t end = min(n, begin + chunk);
+    for (uint32_t k = threadIdx.x; k < 512; k += blockDim.x) sh[k] = 0;
+    if (threadIdx.x == 0) {
+        uint32_t s0 = kNone;
+        if (only_sim >= 0) s0 = (uint32_t)only_sim;
+        else if (begin < end) s0 = (uint32_t)B.pm[cur][begin].w >> M_SIM_SHIFT;
+        s_sim = s0;
+    }
+    __syncthreads();
+    const uint32_t sim0 = s_sim;
+    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        const int4 p = B.pm[cur][i];
+        const uint32_t meta = (uint32_t)p.w;
+        if (meta & (M_DEAD | M_ABSORBED)) continue;
+        const uint32_t s = meta >> M_SIM_SHIFT;
+        if (only_sim >= 0 && s != (uint32_t)only_sim) continue;
+        const SimDev& S = B.sims[s];
+        if (!S.active) continue;
+        const ModelDev& Mo = B.models[S.model];
+        const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
+        uint32_t slot;
+        uint64_t h = 0;
+        if (meta & M_BOUND) {
+            const uint32_t r = (meta & M_RXN) >> M_RXN_SHIFT;
+            slot = Mo.n_sp * Mo.n_comp + r;
+            if (want_digest) {
+                const ReactionDev& R = Mo.rx[r];
+                const uint32_t id = B.aid[cur][i];
+                const uint32_t par = B.apar[cur][i];
+                const bool ra = meta & M_ROLE_A;
+                h = record_hash(id, sp, comp, 1u | (ra ? 4u : 0u), r, p.x, p.y, p.z, par);
+                h += record_hash(par, ra ? R.b : R.a, comp, 2u | (ra ? 0u : 4u), r, p.x, p.y, p.z, id);
+            }
+        } else {
+            slot = sp * Mo.n_comp + comp;
+            if (want_digest) h = record_hash(B.aid[cur][i], sp, comp, 0u, 0xFFu, p.x, p.y, p.z, kNone);
+        }
+        if (s == sim0) atomicAdd(&sh[slot], 1u);
+        else atomicAdd((unsigned long long*)&B.counts[S.counts_off + slot], 1ull);
+        if (want_digest) {
+            // reduce over the threads of the same simulation: one atomic each
+            cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), (int)s);
+            const uint64_t sum = cg::reduce(grp, h, cg::plus<uint64_t>());
+            if (grp.thread_rank() == 0) atomicAdd((unsigned long long*)&B.digests[s], (unsigned long long)sum);
+        }
+    }
+    __syncthreads();
+    if (sim0 != kNone) {
+        const SimDev& S = B.sims[sim0];
+        for (uint32_t k = threadIdx.x; k < S.n_counts; k += blockDim.x)
+            if (sh[k]) atomicAdd((unsigned long long*)&B.counts[S.counts_off + k], (unsigned long long)sh[k]);
+    }
+    if (blockIdx.x == 0) {
+        const uint32_t n_sims = ctl->n_sims;
+        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x) {
+            if (only_sim >= 0 && s != (uint32_t)only_sim) continue;
+            const SimDev& S = B.sims[s];
+            if (!S.active) continue;
+            B.counts[S.counts_off + S.n_counts - 1] = S.next_id;
+            if (want_digest)
+                atomicAdd((unsigned long long*)&B.digests[s],
+                          (unsigned long long)fmix64((uint64_t)S.step | (uint64_t)S.next_id << 32));
+        }
+    }
+}
+
+// k_dump: one record per agent of `sim` (two for a complex), unordered.
+__global__ void __launch_bounds__(kThreads) k_dump(Buffers B, int32_t sim, uint4* out_lo, uint2* out_hi,
+                                                   uint32_t cap) {
+    Ctl* ctl = B.ctl;
+    const uint32_t cur = ctl->cur;
+    const uint32_t n = ctl->n_in;
+    const SimDev& S = B.sims[sim];
+    const ModelDev& Mo = B.models[S.model];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 p = B.pm[cur][i];
+        const uint32_t meta = (uint32_t)p.w;
+        if (meta & (M_DEAD | M_ABSORBED)) continue;
+        if ((meta >> M_SIM_SHIFT) != (uint32_t)sim) continue;
+        const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
+        const uint32_t id = B.aid[cur][i];
+        const bool bound = meta & M_BOUND;
+        const uint32_t k = atomicAdd(&ctl->dump_n, bound ? 2u : 1u);
+        if (k + (bound ? 2u : 1u) > cap) continue;  // host sees dump_n > cap
+        if (bound) {
+            const uint32_t r = (meta & M_RXN) >> M_RXN_SHIFT;
+            const bool ra = meta & M_ROLE_A;
+            const uint32_t par = B.apar[cur][i];
+            const uint32_t hs = ra ? Mo.rx[r].b : Mo.rx[r].a;
+            out_lo[k] = make_uint4(id, sp | comp << 8 | (1u | (ra ? 4u : 0u)) << 16 | r << 24,
+                                   (uint32_t)p.x, (uint32_t)p.y);
+            out_hi[k] = make_uint2((uint32_t)p.z, par);
+            out_lo[k + 1] = make_uint4(par, hs | comp << 8 | (2u | (ra ? 0u : 4u)) << 16 | r << 24,
+                                       (uint32_t)p.x, (uint32_t)p.y);
+            out_hi[k + 1] = make_uint2((uint32_t)p.z, id);
+        } else {
+            out_lo[k] = make_uint4(id, sp | comp << 8 | 0xFFu << 24, (uint32_t)p.x, (uint32_t)p.y);
+            out_hi[k] = make_uint2((uint32_t)p.z, kNone);
+        }
+    }
+}
+
+__global__ void k_debug_philox(const uint4* ctr, const uint2* key, uint4* out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = philox(ctr[i], key[i].x, key[i].y);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s) {
+    k_move<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
+    k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_accept<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_finalize<<<1, 1024, B.cap_births * sizeof(uint64_t), s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev) {
+    cudaEventRecord(ev[0], s);
+    k_move<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    cudaEventRecord(ev[1], s);
+    k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
+    cudaEventRecord(ev[2], s);
+    k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    cudaEventRecord(ev[3], s);
+    k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    cudaEventRecord(ev[4], s);
+    k_accept<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    cudaEventRecord(ev[5], s);
+    k_finalize<<<1, 1024, B.cap_births * sizeof(uint64_t), s>>>(B);
+    cudaEventRecord(ev[6], s);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_kernels(uint32_t cap_births) {
+    return cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(cap_births * sizeof(uint64_t)));
+}
+
+cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim, uint32_t base,
+                        uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp) {
+    if (n0 == 0) return cudaSuccess;
+    k_init<<<L.blocks_agents, kThreads, 0, s>>>(B, sim, base, n0, d_species_end, n_sp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest) {
+    k_observe<<<L.blocks_agents, kThreads, 0, s>>>(B, only_sim, want_digest);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim, void* d_out,
+                        uint32_t cap) {
+    uint4* lo = reinterpret_cast<uint4*>(d_out);
+    uint2* hi = reinterpret_cast<uint2*>(lo + cap);
+    k_dump<<<L.blocks_agents, kThreads, 0, s>>>(B, sim, lo, hi, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
+                                cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_debug_philox<<<blocks, 256, 0, s>>>(reinterpret_cast<const uint4*>(ctr), reinterpret_cast<const uint2*>(key),
+                                          reinterpret_cast<uint4*>(out), n);
+    return cudaGetLastError();
+}
+
+}  // namespace abm

@@ -1,0 +1,242 @@
+"""Engine vs oracle, bit-exact: every config's small case for its full length
+(digest every step, dumps and counts at intervals), full-size prefixes in the
+launch configuration the bench times, and the RNG against cuRAND's device
+Philox.  Tolerance is zero: the state is integer."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_common import assert_same_dump, engine, require_gpu
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def A():
+    require_gpu()
+    return engine()
+
+
+def _curand_lib():
+    d = tempfile.mkdtemp()
+    so = os.path.join(d, "libcurand_philox.so")
+    subprocess.check_call(["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a",
+                           "-shared", "-Xcompiler", "-fPIC", "-o", so,
+                           os.path.join(HERE, "helpers", "curand_philox.cu")])
+    return ctypes.CDLL(so)
+
+
+def test_philox_engine_oracle_curand_device(A, oracle_mod):
+    rng = np.random.default_rng(1234)
+    n = 1 << 16
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:16] = [[i, 0, 0, 0] for i in range(16)]           # small counters too
+    ctr[16:32, 1:] = 0
+    got = A.device_philox(ctr, key)
+    ref = np.zeros_like(ctr)
+    lib = _curand_lib()
+    assert lib.curand_philox_batch(ctr.ctypes.data_as(ctypes.c_void_p), key.ctypes.data_as(ctypes.c_void_p),
+                                   ref.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(n)) == 0
+    assert np.array_equal(got, ref)
+    for i in list(range(40)) + list(rng.integers(0, n, 200)):
+        assert oracle_mod.philox4x32_10(ctr[i].tolist(), key[i].tolist()) == ref[i].tolist()
+
+
+def _lockstep(A, oracle_mod, model, seed, steps, dump_every, digest_every=1, cell_log2=0):
+    g = A.Sim(model, seed, cell_log2=cell_log2)
+    o = oracle_mod.OracleSim(model, seed)
+    try:
+        assert_same_dump(g.dump(), o.dump(), "step 0")
+        assert g.digest() == o.digest()
+        t = 0
+        while t < steps:
+            k = min(digest_every, steps - t)
+            g.step(k)
+            o.step(k)
+            t += k
+            if g.digest() != o.digest():
+                assert_same_dump(g.dump(), o.dump(), f"step {t}")
+                raise AssertionError(f"digest differs at step {t} although dumps agree")
+            if t % dump_every == 0 or t == steps:
+                assert_same_dump(g.dump(), o.dump(), f"step {t}")
+                assert np.array_equal(g.counts(), o.counts()), f"counts at step {t}"
+        assert g.t == o.t == steps
+        return g.counts()
+    finally:
+        g.close()
+        o.close()
+
+
+def test_toy_full_length(A, oracle_mod):
+    c = _lockstep(A, oracle_mod, W.toy(), W.TOY_SEED, W.TOY_STEPS, dump_every=25)
+    assert c[2] > 100                                          # C formed
+
+
+def test_mapk_scaled_parity(A, oracle_mod):
+    c = _lockstep(A, oracle_mod, W.mapk(30_000), W.MAPK_SEED, 400, dump_every=100, digest_every=4)
+    assert c[9:-1].sum() > 0                                  # complexes present
+
+
+def test_nuclear_boosted_parity(A, oracle_mod):
+    m = W.nuclear(30_000, boost=100.0, n_genes=32)
+    c = _lockstep(A, oracle_mod, m, W.NUCLEAR_SEED, 400, dump_every=100, digest_every=4)
+    n_sp, n_c = len(m.species), len(m.compartments)
+    free = c[: n_sp * n_c].reshape(n_sp, n_c)
+    assert free[8].sum() > 0                                   # mRNA born
+    assert c[-1] > m.n_agents                                  # births happened
+
+
+def test_grid_size_does_not_change_results(A, oracle_mod):
+    m = W.mapk(20_000)
+    digests = []
+    for cl in (0, 8, 9, 11):
+        g = A.Sim(m, 5, cell_log2=cl)
+        g.step(50)
+        digests.append(g.digest())
+        g.close()
+    o = oracle_mod.OracleSim(m, 5)
+    o.step(50)
+    assert digests == [o.digest()] * 4
+
+
+def test_mapk_full_size_prefix(A, oracle_mod):
+    """The 1,000,000-agent cascade in the bench's launch configuration."""
+    m = W.mapk(1_000_000)
+    g = A.Sim(m, W.MAPK_SEED)
+    o = oracle_mod.OracleSim(m, W.MAPK_SEED)
+    for t in range(1, 9):
+        g.step(1)
+        o.step(1)
+        assert g.digest() == o.digest(), f"step {t}"
+    assert_same_dump(g.dump(), o.dump(), "step 8")
+    assert np.array_equal(g.counts(), o.counts())
+
+
+def test_nuclear_full_size_prefix(A, oracle_mod):
+    m = W.nuclear(4_000_000)
+    g = A.Sim(m, W.NUCLEAR_SEED)
+    o = oracle_mod.OracleSim(m, W.NUCLEAR_SEED)
+    assert g.digest() == o.digest()
+    for t in range(1, 4):
+        g.step(1)
+        o.step(1)
+        assert g.digest() == o.digest(), f"step {t}"
+    assert np.array_equal(g.counts(), o.counts())
+
+
+def test_batch_members_equal_alone_and_oracle(A, oracle_mod):
+    sims = [(W.mapk(8000 + 3000 * k, drug_frac=0.02 * k), 100 + k) for k in range(4)]
+    sims.append((W.nuclear(12_000, boost=50.0, n_genes=16), 7))
+    sims.append((W.toy(600, 500, edge_um=0.4), 3))
+    cap = sum(m.n_agents for m, _ in sims) * 2 + 100_000
+    b = A.Batch(cap, 4_000_000, 16)
+    ids = [b.add(m, s) for m, s in sims]
+    orcs = [oracle_mod.OracleSim(m, s) for m, s in sims]
+    for t in range(6):
+        b.step(20)
+        for o in orcs:
+            o.step(20)
+        for sid, o in zip(ids, orcs):
+            assert b.digest(sid) == o.digest(), f"sim {sid} step {20 * (t + 1)}"
+    for sid, o in zip(ids, orcs):
+        assert_same_dump(b.dump(sid), o.dump(), f"sim {sid}")
+        assert np.array_equal(b.counts(sid), o.counts())
+    b.close()
+
+
+def test_batch_admission_and_removal_mid_run(A, oracle_mod):
+    m1, m2, m3 = W.mapk(10_000), W.nuclear(9_000, boost=50.0, n_genes=8), W.mapk(7_000, drug_frac=0.0)
+    b = A.Batch(200_000, 2_000_000, 4)
+    s1 = b.add(m1, 11)
+    b.step(30)
+    s2 = b.add(m2, 22)
+    b.step(30)
+    b.remove(s1)
+    b.step(1)
+    s3 = b.add(m3, 33)                                        # may reuse s1's slot
+    b.step(40)
+    o2 = oracle_mod.OracleSim(m2, 22)
+    o2.step(71)
+    o3 = oracle_mod.OracleSim(m3, 33)
+    o3.step(40)
+    assert b.digest(s2) == o2.digest()
+    assert b.digest(s3) == o3.digest()
+    assert_same_dump(b.dump(s3), o3.dump(), "s3")
+    b.close()
+
+
+def test_torch_arena_and_stream(A, oracle_mod):
+    import torch
+    m = W.toy()
+    nbytes = A.arena_bytes(m)
+    arena = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    g = A.Sim(m, 1, arena=arena, stream=stream)
+    g.step(30)
+    o = oracle_mod.OracleSim(m, 1)
+    o.step(30)
+    assert g.digest() == o.digest()
+    g.close()
+
+
+def test_edge_cases(A, oracle_mod):
+    # no agents at all
+    m = W.Model("empty", [W.Species("X", 0, 1.0)], [], [W.Compartment(W.CUBE, 1.0)])
+    g = A.Sim(m, 1)
+    g.step(5)
+    o = oracle_mod.OracleSim(m, 1)
+    o.step(5)
+    assert g.digest() == o.digest() and list(g.counts()) == [0, 0]
+    g.close()
+    # one agent, immobile expressor creating a lineage of mobile dying children
+    m = W.Model("one", [W.Species("G", 1, 0.0, p_emit=0.5, emit=1), W.Species("P", 0, 5.0, p_uni=0.05)], [],
+                [W.Compartment(W.CUBE, 0.2)])
+    _lockstep(A, oracle_mod, m, 9, 300, dump_every=50)
+    # everything dies
+    m = W.Model("die", [W.Species("X", 5000, 1.0, p_uni=0.3)], [], [W.Compartment(W.CUBE, 1.0)])
+    c = _lockstep(A, oracle_mod, m, 2, 60, dump_every=20)
+    assert c[0] == 0
+    # p = 1 everywhere, CONVERT into death of both
+    m = W.Model("burn", [W.Species("A", 3000, 1.0), W.Species("B", 3000, 1.0)],
+                [W.Reaction(0, 1, W.CONVERT, -1, -1, 20.0, 1.0)], [W.Compartment(W.CUBE, 0.5)])
+    _lockstep(A, oracle_mod, m, 4, 80, dump_every=20)
+    # carrier is the acceptor b (smaller D), release kills the proposer
+    m = W.Model("bcar", [W.Species("A", 3000, 5.0), W.Species("B", 3000, 1.0), W.Species("P", 0, 2.0)],
+                [W.Reaction(0, 1, W.BIND, -1, 2, 15.0, 0.7, 0.2)], [W.Compartment(W.CUBE, 0.5)])
+    _lockstep(A, oracle_mod, m, 6, 120, dump_every=30)
+    # ragged: counts not a multiple of any tile, cells not a multiple of 4096
+    m = W.Model("rag", [W.Species("A", 4097, 2.0), W.Species("B", 1, 2.0)],
+                [W.Reaction(0, 1, W.BIND, 0, 1, 30.0, 1.0, 0.5)], [W.Compartment(W.CUBE, 0.77)])
+    _lockstep(A, oracle_mod, m, 8, 100, dump_every=25)
+
+
+def test_births_overflow_is_reported_not_written(A):
+    m = W.Model("flood", [W.Species("G", 20_000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
+                [W.Compartment(W.CUBE, 2.0)])
+    g = A.Sim(m, 1, births_per_step=1024)
+    g.step(1)
+    with pytest.raises(A.AbmError) as e:
+        g.sync()
+    assert e.value.status == A.ECAPACITY
+    with pytest.raises(A.AbmError) as e:
+        g.step(1)
+    assert e.value.status == A.ESTATE
+    g.close()
+
+
+def test_capacity_overflow_is_reported(A):
+    m = W.Model("grow", [W.Species("G", 1000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
+                [W.Compartment(W.CUBE, 2.0)])
+    g = A.Sim(m, 1, capacity=4000)
+    g.step(5)
+    with pytest.raises(A.AbmError) as e:
+        g.counts()
+    assert e.value.status == A.ECAPACITY
+    g.close()
