@@ -337,7 +337,7 @@ class Batch:
             pass
 
 
-N_STEP_KERNELS = 6
+N_STEP_KERNELS = 5
 
 
 def kernel_name(k: int) -> str:

@@ -24,7 +24,7 @@ using namespace abm;
 
 namespace {
 
-constexpr int kTile = 4096;
+constexpr int kTile = kScanTile;
 constexpr size_t kAlign = 256;
 
 // ------------------------------------------------------------------------
@@ -163,8 +163,8 @@ abm_status compile_model(const abm_model* m, Compiled* c, std::string* err) {
         d.thr_cross = threshold(s.p_cross);
         d.uni_to = (int16_t)s.uni_to;
         d.emit = (int16_t)s.emit_species;
-        d.has_event = (d.thr_uni || d.thr_emit) ? 1u : 0u;
-        d.init_comp = (uint32_t)s.compartment;
+        d.has_event = (d.thr_uni || d.thr_emit) ? 1 : 0;
+        d.init_comp = (uint16_t)s.compartment;
         total += s.initial_count;
         c->species_end[i] = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFFFull);
     }
@@ -196,6 +196,7 @@ abm_status compile_model(const abm_model* m, Compiled* c, std::string* err) {
         d.b = (uint8_t)q.b;
         c->dev.rx_of[q.a][q.b] = (uint8_t)r;
         c->dev.sp[q.a].partner_mask |= 1ull << q.b;
+        c->dev.sp[q.a].rmax = std::max<int32_t>(c->dev.sp[q.a].rmax, (int32_t)R);
         c->Rmax = std::max<int64_t>(c->Rmax, R);
     }
     c->dev.n_sp = n_sp;
@@ -238,7 +239,7 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
     const size_t sizes[] = {
         16 * C, 16 * C,                        // pm[2]
         4 * C, 4 * C, 4 * C, 4 * C,            // aid[2], apar[2]
-        8 * C, 8 * C, 4 * C,                   // kr, acc, tgt
+        8 * C, 8 * C, 8 * C,                   // kr, acc, props
         16 * E, 4 * E, 8 * E,                  // extras
         16 * (size_t)Bc, 4 * (size_t)Bc,       // births
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
@@ -486,7 +487,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.apar[1] = (uint32_t*)at();
     B.kr = (uint64_t*)at();
     B.acc = (uint64_t*)at();
-    B.tgt = (uint32_t*)at();
+    B.props = (uint2*)at();
     B.xpm = (int4*)at();
     B.xid = (uint32_t*)at();
     B.xkr = (uint64_t*)at();
@@ -517,8 +518,9 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t want = (b->cap_agents + 255) / 256;
     b->L.threads = 256;
-    b->L.blocks_agents = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 6));
+    b->L.blocks_agents = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 16));
     b->L.blocks_scan = (int)std::max<uint64_t>(1, std::min<uint64_t>(B.n_tiles_max, (uint64_t)sms * 4));
+    b->L.blocks_accept = sms;
 
     std::vector<int16_t> table(65536);
     if (o->ncdf_table) std::memcpy(table.data(), o->ncdf_table, 2 * 65536);
@@ -532,8 +534,9 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
             return destroy_and(ABM_ECUDA);                            \
         }                                                             \
     } while (0)
-    CU(prepare_kernels(births));
+    CU(prepare_kernels());
     CU(cudaMemsetAsync(b->arena, 0, lay.total, b->stream));
+    CU(cudaMemsetAsync(B.acc, 0xFF, 8 * b->cap_agents, b->stream));  // every proposal slot empty
     CU(cudaMemcpyAsync(ztab, table.data(), 2 * 65536, cudaMemcpyHostToDevice, b->stream));
     Ctl c{};
     c.epoch = 1;
@@ -881,7 +884,7 @@ abm_status abm_profile_step(abm_sim* s, uint32_t n, float* kernel_ms, uint32_t n
     return s ? abm_batch_profile_step(s->b, n, kernel_ms, n_kernels) : ABM_EINVAL;
 }
 const char* abm_kernel_name(uint32_t k) {
-    static const char* names[] = {"k_move", "k_scan", "k_scatter", "k_propose", "k_accept", "k_finalize"};
+    static const char* names[] = {"k_move", "k_scan", "k_scatter", "k_propose", "k_accept"};
     return k < (uint32_t)kStepKernels ? names[k] : nullptr;
 }
 abm_status abm_step_index(abm_sim* s, uint32_t* out) {

@@ -6,7 +6,7 @@
 //   apar[2][C]   u32 partner id         (valid for carriers only)
 //   kr[C]        u64 (cell << 32 | rank within cell) from the move pass
 //   acc[C]       u64 proposal slot, min of (dist^2 << 32 | proposer id)
-//   tgt[C]       u32 index of the agent each proposer chose
+//   props[C]     (proposer, target) sorted indices of this step's proposals
 //   xpm/xid/xkr  released partners appended by the move pass (C/2 + 1)
 //   bpm/bpar     births of the step (B)
 //   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
@@ -27,6 +27,7 @@ constexpr int kMaxReactions = 255;
 constexpr int kMaxComp = 4;
 constexpr int kMaxSims = 4096;
 constexpr uint32_t kMaxBirths = 8192;
+constexpr int kScanTile = 8192;           // cells per scan tile (256 threads x 32)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint64_t kInvalidKey = 0xFFFFFFFFFFFFFFFFull;
@@ -57,8 +58,9 @@ struct SpeciesDev {          // 48 bytes
     uint64_t partner_mask;   // bit b: a reaction (this species, b) exists
     uint32_t M;              // Gaussian multiplier, 0 = immobile
     int16_t uni_to, emit;    // -1 = death / none
-    uint32_t has_event;      // thr_uni or thr_emit nonzero
-    uint32_t init_comp;      // compartment of the initial agents
+    uint16_t has_event;      // thr_uni or thr_emit nonzero
+    uint16_t init_comp;      // compartment of the initial agents
+    int32_t rmax;            // largest contact radius over the reactions it proposes
 };
 
 struct ReactionDev {         // 32 bytes
@@ -110,7 +112,10 @@ struct Ctl {
     uint32_t err_info;
     uint32_t n_sims;         // sim slots in use (upper bound of the table)
     uint32_t dump_n;
-    uint32_t pad[4];
+    uint32_t pad0;
+    uint32_t blocks_done;    // blocks of k_accept finished this step
+    uint32_t n_props;        // proposals of this step (list in props)
+    uint32_t pad;
 };
 
 struct Buffers {
@@ -119,7 +124,7 @@ struct Buffers {
     uint32_t* apar[2];
     uint64_t* kr;
     uint64_t* acc;
-    uint32_t* tgt;
+    uint2* props;
     int4* xpm;
     uint32_t* xid;
     uint64_t* xkr;
@@ -222,15 +227,16 @@ struct Launch {
     int blocks_agents;       // grid of the per-agent kernels (grid-stride)
     int threads;             // 256
     int blocks_scan;
+    int blocks_accept;       // CTAs of the acceptance kernel (walks the proposal list)
 };
 
-cudaError_t prepare_kernels(uint32_t cap_births);
+cudaError_t prepare_kernels();
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s);
 cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim,
                         uint32_t base, uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp);
 cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest);
-// The step with a CUDA event before and after each of its kernels (ev[0..6]).
-constexpr int kStepKernels = 6;
+// The step with a CUDA event before and after each of its kernels (ev[0..5]).
+constexpr int kStepKernels = 5;
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim, void* d_out,
                         uint32_t cap);

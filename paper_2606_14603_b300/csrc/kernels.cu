@@ -1,16 +1,17 @@
 // kernels.cu — the per-step CUDA kernels (sm_103a) of the molecule-agent engine.
 //
 // One step (paper Sec. 2: diffusion, proximity binding, product release,
-// expression, degradation, compartment migration) is six launches over the
+// expression, degradation, compartment migration) is five launches over the
 // whole batch of simulations, all reading their sizes from the device
 // control block so that a captured CUDA graph replays them unchanged:
 //
 //   k_move      P1 events + P2 Brownian move + cell key + histogram rank
 //   k_scan      exclusive scan of the cell histogram (decoupled look-back)
 //   k_scatter   reorder every live agent by cell into the other buffer
-//   k_propose   27-cell neighbour query, nearest eligible partner, atomicMin
-//   k_accept    final-edge rule and reaction application
-//   k_finalize  births (ids ranked by parent id), per-step bookkeeping
+//   k_propose   neighbour query over the cells a contact radius can reach,
+//               nearest eligible partner, atomicMin on a packed key
+//   k_accept    final-edge rule and reaction application; its last block
+//               runs the births (ids ranked by parent id) and bookkeeping
 //
 // The engine never depends on storage order: every decision is a function
 // of the set of (id, state) pairs, so atomics may run in any order.
@@ -26,8 +27,7 @@ namespace abm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kScanV = 16;
-constexpr int kTile = kThreads * kScanV;  // 4096 cells per scan tile
+constexpr int kScanV = kScanTile / kThreads;  // 32 cells per thread
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
@@ -96,6 +96,10 @@ __global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
     int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
     const uint32_t* __restrict__ apar = B.apar[cur];
+    // proposal slots touched last step become empty again (the list is short)
+    const uint32_t np = ctl->n_props;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x)
+        B.acc[B.props[k].y] = kEmpty;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int4 p = pm[i];
         uint32_t meta = (uint32_t)p.w;
@@ -189,9 +193,9 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
     const uint32_t n = ctl->n_cells;
-    const uint32_t ntiles = (n + kTile - 1) / kTile;
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
     const uint64_t epoch = (uint64_t)(ctl->epoch & 0x3FFFFFFFu);
-    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_tile, s_prefix, s_first;
     __shared__ uint32_t s_warp[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= ntiles) return;
-        const uint32_t base = tile * kTile + threadIdx.x * kScanV;
+        const uint32_t base = tile * kScanTile + threadIdx.x * kScanV;
         uint32_t v[kScanV];
         uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
 #pragma unroll
@@ -231,32 +235,52 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
             total += sw;
         }
         const uint32_t texcl = wpre + incl - tsum;
-        if (threadIdx.x == 0) {
-            uint64_t* desc = B.tiles + tile;
-            uint32_t excl = 0;
-            if (tile == 0) {
-                st_release(desc, epoch << 34 | 2ull << 32 | total);
-            } else {
-                st_release(desc, epoch << 34 | 1ull << 32 | total);
-                int64_t k = (int64_t)tile - 1;
+        // publish the aggregate, then look back over up to 256 predecessor
+        // tiles per round (thread j reads tile k - j); the nearest tile that
+        // holds an inclusive prefix ends the walk
+        uint64_t* desc = B.tiles + tile;
+        if (threadIdx.x == 0) st_release(desc, epoch << 34 | (tile == 0 ? 2ull : 1ull) << 32 | total);
+        uint32_t excl = 0;
+        int64_t k = (int64_t)tile - 1;
+        bool timed_out = false;
+        while (k >= 0) {
+            const int64_t idx = k - threadIdx.x;
+            uint32_t st = 2, val = 0;
+            if (idx >= 0) {
                 uint32_t spins = 0;
-                while (k >= 0) {
-                    const uint64_t d = ld_acquire(B.tiles + k);
-                    const uint32_t st = (uint32_t)(d >> 32) & 3u;
-                    if ((d >> 34) != epoch || st == 0) {
-                        if (++spins > kSpinLimit) {
-                            raise_error(ctl, ERR_TIMEOUT_SCAN, tile);
-                            break;
-                        }
-                        __nanosleep(32);
-                        continue;
+                for (;;) {
+                    const uint64_t d = ld_acquire(B.tiles + idx);
+                    st = (uint32_t)(d >> 32) & 3u;
+                    val = (uint32_t)d;
+                    if ((d >> 34) == epoch && st != 0) break;
+                    if (++spins > kSpinLimit) {
+                        timed_out = true;
+                        st = 2;
+                        val = 0;
+                        break;
                     }
-                    excl += (uint32_t)d;
-                    if (st == 2) break;
-                    k--;
+                    __nanosleep(32);
                 }
-                st_release(desc, epoch << 34 | 2ull << 32 | (excl + total));
             }
+            if (threadIdx.x == 0) s_first = kThreads;
+            __syncthreads();
+            if (st == 2) atomicMin(&s_first, (uint32_t)threadIdx.x);
+            __syncthreads();
+            const uint32_t first = s_first;
+            uint32_t part = threadIdx.x <= first ? val : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+            if (lane == 0) s_warp[warp] = part;
+            __syncthreads();
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; w++) excl += s_warp[w];
+            __syncthreads();
+            if (first < (uint32_t)kThreads) break;
+            k -= kThreads;
+        }
+        if (timed_out) raise_error(ctl, ERR_TIMEOUT_SCAN, tile);
+        if (threadIdx.x == 0) {
+            if (tile != 0) st_release(desc, epoch << 34 | 2ull << 32 | (excl + total));
             s_prefix = excl;
         }
         __syncthreads();
@@ -282,12 +306,13 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
 
 // ------------------------------------------------------------------------
 // k_scatter: every live agent (and every released partner) to its slot
-// start[cell] + rank in the other buffer; clears its proposal slot.
+// start[cell] + rank in the other buffer.
 __global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
     const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
     const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_props = 0;  // k_move has consumed the old list
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
         uint64_t kr;
         int4 p;
@@ -312,15 +337,58 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
         B.pm[nxt][dest] = p;
         B.aid[nxt][dest] = id;
         if ((uint32_t)p.w & M_BOUND) B.apar[nxt][dest] = par;
-        B.acc[dest] = kEmpty;
     }
 }
 
 // ------------------------------------------------------------------------
-// k_propose: each free agent of a proposing species looks at the 27 cells
-// around its own (three x-contiguous ranges per (dy, dz) row), keeps the
-// nearest eligible partner by (dist^2, id), and claims it with atomicMin on
-// the partner's slot using the key (dist^2 << 32 | own id).
+// One candidate q (sorted index gj) for proposer p: keep the nearest eligible
+// partner by (dist^2, id); the pair draw is taken only when it could win.
+struct Best {
+    uint64_t key = kEmpty;
+    uint32_t target = kNone;
+};
+
+__device__ __forceinline__ void consider(const SimDev& S, const ModelDev& Mo, const int4& p, uint32_t meta,
+                                         uint32_t sp, uint64_t mask, int rmax, uint32_t& ida, uint32_t gi,
+                                         const int4& q, uint32_t gj, const uint32_t* __restrict__ aid,
+                                         uint32_t t, Best& best) {
+    // cheap rejections first: almost every candidate is beyond every radius
+    const int dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+    if (abs(dx) > rmax || abs(dy) > rmax || abs(dz) > rmax) return;
+    const uint32_t mq = (uint32_t)q.w;
+    if (mq & M_BOUND) return;
+    if ((mq ^ meta) & M_COMP) return;
+    const uint32_t spb = mq & M_SP;
+    if (!((mask >> spb) & 1ull)) return;
+    const ReactionDev& R = Mo.rx[Mo.rx_of[sp][spb]];
+    if (abs(dx) > R.R || abs(dy) > R.R || abs(dz) > R.R) return;
+    const uint32_t d2 = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+    if (d2 > R.R2) return;
+    const uint32_t idb = aid[gj];
+    const uint64_t key = (uint64_t)d2 << 32 | idb;
+    if (key >= best.key) return;  // cannot win: the draw is not needed
+    if (ida == kNone) ida = aid[gi];
+    const uint32_t lo = min(ida, idb), hi = max(ida, idb);
+    const uint4 u = philox(make_uint4(lo, hi, t, 1u), S.key0, S.key1);
+    if ((uint64_t)u.x >= R.thr_bind) return;
+    best.key = key;
+    best.target = gj;
+}
+
+__device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida, uint32_t gi) {
+    if (best.target == kNone) return;
+    atomicMin((unsigned long long*)&B.acc[best.target], (unsigned long long)((best.key & 0xFFFFFFFF00000000ull) | ida));
+    const uint32_t k = reserve(&B.ctl->n_props);  // k < capacity: at most one proposal per agent
+    B.props[k] = make_uint2(gi, best.target);
+}
+
+// ------------------------------------------------------------------------
+// k_propose: every free agent of a proposing species scans the cells that
+// intersect the box [p - rmax, p + rmax] (rmax: its largest contact radius)
+// -- one or two cells per axis, x-consecutive cells forming one contiguous
+// range of the cell-sorted array -- keeps the nearest eligible partner by
+// (dist^2, id) and claims it with atomicMin.  Any partner within a contact
+// radius lies inside that box, so the result equals the 27-cell search.
 __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
@@ -329,77 +397,125 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     const int4* __restrict__ pm = B.pm[nxt];
     const uint32_t* __restrict__ aid = B.aid[nxt];
     const uint32_t* __restrict__ start = B.start;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int4 p = pm[i];
+    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < n; gi += gridDim.x * blockDim.x) {
+        const int4 p = pm[gi];
         const uint32_t meta = (uint32_t)p.w;
-        uint32_t target = kNone;
-        if (!(meta & M_BOUND)) {
-            const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
-            const ModelDev& Mo = B.models[S.model];
-            const uint32_t sp = meta & M_SP;
-            const uint64_t mask = Mo.sp[sp].partner_mask;
-            if (mask) {
-                const uint32_t ida = aid[i];
-                const uint32_t t = S.step;
-                const int g = (int)S.g;
-                const int sh = (int)S.shift;
-                const int cx = p.x >> sh, cy = p.y >> sh, cz = p.z >> sh;
-                const int x0 = cx > 0 ? cx - 1 : 0;
-                const int x1 = cx < g - 1 ? cx + 1 : g - 1;
-                uint64_t best = kEmpty;
-                for (int zz = cz - 1; zz <= cz + 1; zz++) {
-                    if (zz < 0 || zz >= g) continue;
-                    for (int yy = cy - 1; yy <= cy + 1; yy++) {
-                        if (yy < 0 || yy >= g) continue;
-                        const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
-                        const uint32_t j1 = start[row + x1 + 1];
-                        for (uint32_t j = start[row + x0]; j < j1; j++) {
-                            if (j == i) continue;
-                            const int4 q = pm[j];
-                            const uint32_t mq = (uint32_t)q.w;
-                            if (mq & M_BOUND) continue;
-                            if ((mq ^ meta) & M_COMP) continue;
-                            const uint32_t spb = mq & M_SP;
-                            if (!((mask >> spb) & 1ull)) continue;
-                            const ReactionDev& R = Mo.rx[Mo.rx_of[sp][spb]];
-                            const int dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-                            if (abs(dx) > R.R || abs(dy) > R.R || abs(dz) > R.R) continue;
-                            const uint32_t d2 = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-                            if (d2 > R.R2) continue;
-                            const uint32_t idb = aid[j];
-                            const uint64_t key = (uint64_t)d2 << 32 | idb;
-                            if (key >= best) continue;
-                            const uint32_t lo = min(ida, idb), hi = max(ida, idb);
-                            const uint4 u = philox(make_uint4(lo, hi, t, 1u), S.key0, S.key1);
-                            if ((uint64_t)u.x >= R.thr_bind) continue;
-                            best = key;
-                            target = j;
-                        }
-                    }
-                }
-                if (target != kNone) atomicMin((unsigned long long*)&B.acc[target],
-                                               (unsigned long long)((best & 0xFFFFFFFF00000000ull) | ida));
+        if (meta & M_BOUND) continue;
+        const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+        const ModelDev& Mo = B.models[S.model];
+        const uint32_t sp = meta & M_SP;
+        const uint64_t mask = Mo.sp[sp].partner_mask;
+        if (!mask) continue;
+        const int rmax = Mo.sp[sp].rmax;
+        const int g = (int)S.g, sh = (int)S.shift;
+        const int xlo = max((p.x - rmax) >> sh, 0), xhi = min((p.x + rmax) >> sh, g - 1);
+        const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
+        const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
+        Best best;
+        uint32_t ida = kNone;
+        for (int zz = zlo; zz <= zhi; zz++)
+            for (int yy = ylo; yy <= yhi; yy++) {
+                const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
+                const uint32_t j1 = start[row + xhi + 1];
+                for (uint32_t j = start[row + xlo]; j < j1; j++)
+                    if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
             }
-        }
-        B.tgt[i] = target;
+        claim(B, best, ida, gi);
     }
 }
 
 // ------------------------------------------------------------------------
-// k_accept: edge i -> j is final iff j's slot holds i's id and nobody
-// proposed to i.  Final edges are disjoint, so each is applied by its
-// proposer without further synchronisation.
+// Births and per-step bookkeeping, run by the last block of k_accept:
+// newborns get ids next_id + rank, the rank ordering the births of the same
+// simulation by parent id, and are appended after the sorted agents; then
+// the buffer flips and every active simulation's step counter advances.
+constexpr int kKeyTile = 1024;
+
+__device__ void finalize_block(Buffers& B) {
+    __shared__ uint64_t s_key[kKeyTile];
+    Ctl* ctl = B.ctl;
+    const uint32_t nxt = ctl->cur ^ 1u;
+    const uint32_t ns = ctl->n_sorted;
+    uint32_t nb = ld_volatile(&ctl->n_births);
+    if (nb > B.cap_births) nb = B.cap_births;  // the overflow was already flagged
+    if (nb && (uint64_t)ns + nb > B.cap_agents) {
+        if (threadIdx.x == 0) raise_error(ctl, ERR_CAPACITY_AGENTS, ns + nb);
+        return;
+    }
+    // key of birth k: simulation in the high word, parent id in the low word
+    auto key_of = [&](uint32_t k) -> uint64_t {
+        return (uint64_t)((uint32_t)B.bpm[k].w >> M_SIM_SHIFT) << 32 | B.bpar[k];
+    };
+    // rank of each birth among the births of its simulation (ids are unique:
+    // at most one birth per parent per step), and whether it is the last one
+    const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+    constexpr int kMaxPer = (kMaxBirths + kThreads - 1) / kThreads;
+    uint32_t lt[kMaxPer], gt[kMaxPer];
+    uint64_t mine[kMaxPer];
+    for (uint32_t q = 0; q < per; q++) {
+        const uint32_t k = threadIdx.x + q * blockDim.x;
+        mine[q] = k < nb ? key_of(k) : 0;
+        lt[q] = gt[q] = 0;
+    }
+    for (uint32_t base = 0; base < nb; base += kKeyTile) {
+        const uint32_t m = min((uint32_t)kKeyTile, nb - base);
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) s_key[j] = key_of(base + j);
+        __syncthreads();
+        for (uint32_t q = 0; q < per; q++) {
+            const uint64_t key = mine[q];
+            for (uint32_t j = 0; j < m; j++) {
+                const uint64_t o = s_key[j];
+                const bool same = (o >> 32) == (key >> 32);
+                lt[q] += same & (o < key);
+                gt[q] += same & (o > key);
+            }
+        }
+    }
+    for (uint32_t q = 0; q < per; q++) {
+        const uint32_t k = threadIdx.x + q * blockDim.x;
+        if (k >= nb) continue;
+        const uint32_t s = (uint32_t)(mine[q] >> 32);
+        const uint64_t nid = (uint64_t)B.sims[s].next_id + lt[q];
+        if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
+        B.pm[nxt][ns + k] = B.bpm[k];
+        B.aid[nxt][ns + k] = (uint32_t)nid;
+    }
+    __syncthreads();
+    for (uint32_t q = 0; q < per; q++) {
+        const uint32_t k = threadIdx.x + q * blockDim.x;
+        if (k < nb && gt[q] == 0) B.sims[mine[q] >> 32].next_id += lt[q] + 1;  // one writer per sim
+    }
+    const uint32_t n_sims = ctl->n_sims;
+    for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
+        if (B.sims[s].active) B.sims[s].step += 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->n_in = ns + nb;
+        ctl->n_extra = 0;
+        ctl->n_births = 0;
+        ctl->cur = nxt;
+        ctl->epoch = ctl->epoch + 1;
+    }
+}
+
+// ------------------------------------------------------------------------
+// k_accept: walks the proposal list; edge i -> j is final iff j's slot holds
+// i's id and nobody proposed to i.  Final edges are disjoint, so each is
+// applied without further synchronisation.  The last block to finish runs
+// the births and the step's bookkeeping.
 __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
+    __shared__ bool s_last;
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
     const uint32_t nxt = ctl->cur ^ 1u;
-    const uint32_t n = ctl->n_sorted;
+    const uint32_t np = ctl->n_props;
     int4* __restrict__ pm = B.pm[nxt];
     uint32_t* __restrict__ aid = B.aid[nxt];
     uint32_t* __restrict__ apar = B.apar[nxt];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t j = B.tgt[i];
-        if (j == kNone) continue;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        const uint2 e = B.props[k];
+        const uint32_t i = e.x, j = e.y;
         const uint64_t kb = B.acc[j];
         const uint32_t ida = aid[i];
         if ((uint32_t)kb != ida || B.acc[i] != kEmpty) continue;
@@ -425,63 +541,15 @@ __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
         *wa = ma;
         *wb = mb;
     }
-}
-
-// ------------------------------------------------------------------------
-// k_finalize (one block): newborns get ids next_id + rank, the rank ordering
-// births of the same simulation by parent id, and are appended after the
-// sorted agents; then the step's bookkeeping (buffer flip, step counters).
-__global__ void __launch_bounds__(1024) k_finalize(Buffers B) {
-    extern __shared__ uint64_t s_key[];
-    Ctl* ctl = B.ctl;
-    if (ld_volatile(&ctl->err)) return;
-    const uint32_t nxt = ctl->cur ^ 1u;
-    const uint32_t ns = ctl->n_sorted;
-    uint32_t nb = ctl->n_births;
-    if (nb > B.cap_births) nb = B.cap_births;  // the overflow was already flagged
-    if (nb && (uint64_t)ns + nb > B.cap_agents) {
-        if (threadIdx.x == 0) raise_error(ctl, ERR_CAPACITY_AGENTS, ns + nb);
-        return;
-    }
-    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x)
-        s_key[k] = (uint64_t)((uint32_t)B.bpm[k].w >> M_SIM_SHIFT) << 32 | B.bpar[k];
+    // last-block-done: every block's writes are visible to the last one
+    __threadfence();
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
-        const uint64_t key = s_key[k];
-        uint32_t lt = 0;
-        for (uint32_t j = 0; j < nb; j++) {
-            const uint64_t o = s_key[j];
-            lt += ((o >> 32) == (key >> 32)) & (o < key);
-        }
-        const uint32_t s = (uint32_t)(key >> 32);
-        const uint64_t nid = (uint64_t)B.sims[s].next_id + lt;
-        if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
-        B.pm[nxt][ns + k] = B.bpm[k];
-        B.aid[nxt][ns + k] = (uint32_t)nid;
-    }
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1;
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) {
-        const uint64_t key = s_key[k];
-        uint32_t lt = 0, gt = 0;
-        for (uint32_t j = 0; j < nb; j++) {
-            const uint64_t o = s_key[j];
-            const bool same = (o >> 32) == (key >> 32);
-            lt += same & (o < key);
-            gt += same & (o > key);
-        }
-        if (gt == 0) B.sims[key >> 32].next_id += lt + 1;  // one writer per sim
-    }
-    const uint32_t n_sims = ctl->n_sims;
-    for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
-        if (B.sims[s].active) B.sims[s].step += 1;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ctl->n_in = ns + nb;
-        ctl->n_extra = 0;
-        ctl->n_births = 0;
-        ctl->cur = nxt;
-        ctl->epoch = ctl->epoch + 1;
-    }
+    if (!s_last) return;
+    __threadfence();
+    finalize_block(B);
+    if (threadIdx.x == 0) ctl->blocks_done = 0;
 }
 
 // ------------------------------------------------------------------------
@@ -644,8 +712,7 @@ cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s) {
     k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
     k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
     k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
-    k_accept<<<L.blocks_agents, kThreads, 0, s>>>(B);
-    k_finalize<<<1, 1024, B.cap_births * sizeof(uint64_t), s>>>(B);
+    k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
     return cudaGetLastError();
 }
 
@@ -659,17 +726,12 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
     cudaEventRecord(ev[3], s);
     k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[4], s);
-    k_accept<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[5], s);
-    k_finalize<<<1, 1024, B.cap_births * sizeof(uint64_t), s>>>(B);
-    cudaEventRecord(ev[6], s);
     return cudaGetLastError();
 }
 
-cudaError_t prepare_kernels(uint32_t cap_births) {
-    return cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(cap_births * sizeof(uint64_t)));
-}
+cudaError_t prepare_kernels() { return cudaSuccess; }
 
 cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim, uint32_t base,
                         uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp) {

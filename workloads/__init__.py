@@ -161,10 +161,11 @@ NUC_SPECIES = ["ppMEK", "ERK", "ppERK", "PPase", "Elk1", "pElk1", "GENE_off", "G
 
 
 def nuclear(n_total: int = 4_000_000, cell_um: float | None = None, boost: float = 1.0,
-            n_genes: int = 64, dt_s: float = 1e-6) -> Model:
-    """The two-compartment network.  `boost` multiplies the first-order and
-    emission probabilities (capped at 1) so that small parity cases see many
-    events; boost = 1 is the nominal model."""
+            n_genes: int = 64, genes_on: int = 0, dt_s: float = 1e-6) -> Model:
+    """The two-compartment network.  `boost` multiplies the first-order,
+    emission and membrane-crossing probabilities (capped at 1) so that small
+    parity cases see many events; boost = 1 is the nominal model.  `genes_on`
+    of the gene sites start active (the nominal model starts with all off)."""
     if cell_um is None:
         cell_um = 12.0 * (n_total / 4_000_000) ** (1.0 / 3.0)
     nuc_um = cell_um * 5.0 / 12.0
@@ -175,22 +176,23 @@ def nuclear(n_total: int = 4_000_000, cell_um: float | None = None, boost: float
         _N_ERK: int(round(1_600_000 * scale)),
         _N_PPERK: int(round(400_000 * scale)),
         _N_PPASE: int(round(1_400_000 * scale)),
-        _N_GOFF: n_genes,
+        _N_GOFF: n_genes - genes_on,
+        _N_GON: genes_on,
     }
     counts[_N_ELK] = n_total - sum(counts.values())
     sp = [
         Species("ppMEK", counts[_N_PPMEK], 3.0, 0),
-        Species("ERK", counts[_N_ERK], 4.0, 0, p_cross=1e-3),
-        Species("ppERK", counts[_N_PPERK], 4.0, 0, p_cross=1e-3),
-        Species("PPase", counts[_N_PPASE], 2.0, 0, p_cross=1e-3),
+        Species("ERK", counts[_N_ERK], 4.0, 0, p_cross=b(1e-3)),
+        Species("ppERK", counts[_N_PPERK], 4.0, 0, p_cross=b(1e-3)),
+        Species("PPase", counts[_N_PPASE], 2.0, 0, p_cross=b(1e-3)),
         Species("Elk1", counts[_N_ELK], 3.0, 1),
         Species("pElk1", 0, 3.0, 1),
         Species("GENE_off", counts[_N_GOFF], 0.0, 1),
-        Species("GENE_on", 0, 0.0, 1, p_uni=b(1e-4), uni_to=_N_GOFF, p_emit=b(1e-2), emit=_N_MRNA),
-        Species("mRNA", 0, 1.0, 1, p_cross=1e-2, p_uni=b(1e-4), uni_to=-1, p_emit=b(1e-3), emit=_N_CFOS),
-        Species("cFos", 0, 3.0, 1, p_cross=1e-3, p_uni=b(2e-5), uni_to=-1),
-        Species("pcFos", 0, 3.0, 1, p_cross=1e-3, p_uni=b(5e-6), uni_to=-1, p_emit=b(1e-4), emit=_N_F),
-        Species("F", 0, 2.0, 1, p_cross=1e-3, p_uni=b(1e-5), uni_to=-1),
+        Species("GENE_on", counts[_N_GON], 0.0, 1, p_uni=b(1e-4), uni_to=_N_GOFF, p_emit=b(1e-2), emit=_N_MRNA),
+        Species("mRNA", 0, 1.0, 1, p_cross=b(1e-2), p_uni=b(1e-4), uni_to=-1, p_emit=b(1e-3), emit=_N_CFOS),
+        Species("cFos", 0, 3.0, 1, p_cross=b(1e-3), p_uni=b(2e-5), uni_to=-1),
+        Species("pcFos", 0, 3.0, 1, p_cross=b(1e-3), p_uni=b(5e-6), uni_to=-1, p_emit=b(1e-4), emit=_N_F),
+        Species("F", 0, 2.0, 1, p_cross=b(1e-3), p_uni=b(1e-5), uni_to=-1),
     ]
     rx = [
         Reaction(_N_PPMEK, _N_ERK, BIND, _N_PPMEK, _N_PPERK, 4.0, 0.3, 0.05),
