@@ -283,16 +283,10 @@ def main():
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     n_agents = 0.5 * (n_before + n_after)
-    sd = None
-    # cells of the simulation grid for per-cell kernels
-    import workloads as W  # noqa: F401
-    gx = None
     bpu, unit_name = KERNEL_BYTES[dom]
-    ext = model.compartments[0].size_um * 1000 / model.unit_nm
-    cell_log2 = int(os.environ.get("ABM_CELL_LOG2", "0"))
     units = n_agents
     if unit_name == "cell":
-        units = (int(round(ext)) // 1024 + 1) ** 3
+        units = sim.grid_cells()
     dom_ms = prof[dom] / P
     achieved = bpu * units / (dom_ms / 1e3) / 1e9
     traffic = ncu_traffic(dom)
@@ -322,7 +316,8 @@ def main():
         el = time.perf_counter() - t0
         s2.close()
         n_counts = len(cvec)
-        model_bytes = len(model.species) * 48 + len(model.reactions) * 48 + len(model.compartments) * 48 + 2 * 65536
+        # host-to-device at creation: Gaussian table, integer model tables, sim entry, control words
+        model_bytes = 2 * 65536 + 15376 + 512
         e2e = {"value": molecules(cvec, model) * Ke / el, "unit": UNIT,
                "h2d_bytes_per_step": model_bytes / Ke, "d2h_bytes_per_step": 8 * n_counts,
                "steps": Ke, "includes": "abm_create (model upload, device-side placement) + per step "

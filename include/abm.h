@@ -159,6 +159,8 @@ abm_status  abm_digest(abm_sim* sim, uint64_t* out);
 abm_status  abm_dump(abm_sim* sim, abm_record* out, size_t cap, size_t* n_out);
 abm_status  abm_sync(abm_sim* sim);
 abm_status  abm_step_index(abm_sim* sim, uint32_t* out);
+/* Number of grid cells of the simulation (host-side value, no device work). */
+abm_status  abm_grid_cells(abm_sim* sim, uint64_t* out);
 const char* abm_last_error(const abm_sim* sim);
 void        abm_destroy(abm_sim* sim);        /* NULL-safe */
 

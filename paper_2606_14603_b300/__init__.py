@@ -107,6 +107,7 @@ def lib():
             "abm_profile_step": (C.c_int, [P, C.c_uint32, P, C.c_uint32]),
             "abm_batch_profile_step": (C.c_int, [P, C.c_uint32, P, C.c_uint32]),
             "abm_kernel_name": (C.c_char_p, [C.c_uint32]),
+            "abm_grid_cells": (C.c_int, [P, C.POINTER(C.c_uint64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -220,6 +221,12 @@ class Sim:
         ms = np.zeros(8, dtype=np.float32)
         _check(lib().abm_profile_step(self._h, n, ms.ctypes.data, 8), lib().abm_last_error, self._h)
         return {kernel_name(k): float(ms[k]) for k in range(N_STEP_KERNELS)}
+
+    def grid_cells(self) -> int:
+        """Cells of this simulation's grid."""
+        v = C.c_uint64()
+        _check(lib().abm_grid_cells(self._h, C.byref(v)), lib().abm_last_error, self._h)
+        return v.value
 
     @property
     def t(self) -> int:

@@ -895,6 +895,11 @@ abm_status abm_step_index(abm_sim* s, uint32_t* out) {
     CU(cudaMemcpy(out, &b->B.sims[s->id].step, 4, cudaMemcpyDeviceToHost));
     return ABM_OK;
 }
+abm_status abm_grid_cells(abm_sim* s, uint64_t* out) {
+    if (!s || !out) return ABM_EINVAL;
+    *out = s->b->sims[s->id].n_cells;
+    return ABM_OK;
+}
 const char* abm_last_error(const abm_sim* s) { return s ? abm_batch_last_error(s->b) : "null handle"; }
 void abm_destroy(abm_sim* s) {
     if (!s) return;

@@ -306,37 +306,53 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
 
 // ------------------------------------------------------------------------
 // k_scatter: every live agent (and every released partner) to its slot
-// start[cell] + rank in the other buffer.
+// start[cell] + rank in the other buffer.  Each thread moves four agents,
+// issuing all loads before the dependent start[] gathers.
+constexpr int kScatterILP = 4;
+
 __global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
     const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
     const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_props = 0;  // k_move has consumed the old list
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
-        uint64_t kr;
-        int4 p;
-        uint32_t id, par = kNone;
-        if (j < n_in) {
-            kr = B.kr[j];
-            if (kr == kInvalidKey) continue;
-            p = B.pm[cur][j];
-            id = B.aid[cur][j];
-            if ((uint32_t)p.w & M_BOUND) par = B.apar[cur][j];
-        } else {
-            const uint32_t k = j - n_in;
-            kr = B.xkr[k];
-            p = B.xpm[k];
-            id = B.xid[k];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < total; j0 += kScatterILP * stride) {
+        uint64_t kr[kScatterILP];
+        int4 p[kScatterILP];
+        uint32_t id[kScatterILP], par[kScatterILP];
+#pragma unroll
+        for (int u = 0; u < kScatterILP; u++) {
+            const uint32_t j = j0 + u * stride;
+            kr[u] = kInvalidKey;
+            par[u] = kNone;
+            if (j < n_in) {
+                kr[u] = B.kr[j];
+                p[u] = B.pm[cur][j];
+                id[u] = B.aid[cur][j];
+                par[u] = B.apar[cur][j];
+            } else if (j < total) {
+                const uint32_t k = j - n_in;
+                kr[u] = B.xkr[k];
+                p[u] = B.xpm[k];
+                id[u] = B.xid[k];
+            }
         }
-        const uint32_t dest = B.start[kr >> 32] + (uint32_t)kr;
-        if (dest >= B.cap_agents) {
-            raise_error(ctl, ERR_CAPACITY_AGENTS, dest);
-            continue;
+        uint32_t dest[kScatterILP];
+#pragma unroll
+        for (int u = 0; u < kScatterILP; u++)
+            dest[u] = kr[u] == kInvalidKey ? kNone : B.start[kr[u] >> 32] + (uint32_t)kr[u];
+#pragma unroll
+        for (int u = 0; u < kScatterILP; u++) {
+            if (dest[u] == kNone) continue;
+            if (dest[u] >= B.cap_agents) {
+                raise_error(ctl, ERR_CAPACITY_AGENTS, dest[u]);
+                continue;
+            }
+            B.pm[nxt][dest[u]] = p[u];
+            B.aid[nxt][dest[u]] = id[u];
+            if ((uint32_t)p[u].w & M_BOUND) B.apar[nxt][dest[u]] = par[u];
         }
-        B.pm[nxt][dest] = p;
-        B.aid[nxt][dest] = id;
-        if ((uint32_t)p.w & M_BOUND) B.apar[nxt][dest] = par;
     }
 }
 
@@ -383,13 +399,17 @@ __device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida
 }
 
 // ------------------------------------------------------------------------
-// k_propose: every free agent of a proposing species scans the cells that
-// intersect the box [p - rmax, p + rmax] (rmax: its largest contact radius)
+// k_propose: every free agent of a proposing species (compacted per block
+// from 1024 consecutive sorted agents) scans the cells that intersect the box [p - rmax, p + rmax] (rmax: its largest contact radius)
 // -- one or two cells per axis, x-consecutive cells forming one contiguous
 // range of the cell-sorted array -- keeps the nearest eligible partner by
 // (dist^2, id) and claims it with atomicMin.  Any partner within a contact
 // radius lies inside that box, so the result equals the 27-cell search.
+constexpr int kProposeChunk = 4 * kThreads;  // sorted agents examined per block round
+
 __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
+    __shared__ uint32_t s_list[kProposeChunk];
+    __shared__ uint32_t s_n;
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
     const uint32_t nxt = ctl->cur ^ 1u;
@@ -397,30 +417,55 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     const int4* __restrict__ pm = B.pm[nxt];
     const uint32_t* __restrict__ aid = B.aid[nxt];
     const uint32_t* __restrict__ start = B.start;
-    for (uint32_t gi = blockIdx.x * blockDim.x + threadIdx.x; gi < n; gi += gridDim.x * blockDim.x) {
-        const int4 p = pm[gi];
-        const uint32_t meta = (uint32_t)p.w;
-        if (meta & M_BOUND) continue;
-        const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
-        const ModelDev& Mo = B.models[S.model];
-        const uint32_t sp = meta & M_SP;
-        const uint64_t mask = Mo.sp[sp].partner_mask;
-        if (!mask) continue;
-        const int rmax = Mo.sp[sp].rmax;
-        const int g = (int)S.g, sh = (int)S.shift;
-        const int xlo = max((p.x - rmax) >> sh, 0), xhi = min((p.x + rmax) >> sh, g - 1);
-        const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
-        const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
-        Best best;
-        uint32_t ida = kNone;
-        for (int zz = zlo; zz <= zhi; zz++)
-            for (int yy = ylo; yy <= yhi; yy++) {
-                const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
-                const uint32_t j1 = start[row + xhi + 1];
-                for (uint32_t j = start[row + xlo]; j < j1; j++)
-                    if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * kProposeChunk; base < n; base += gridDim.x * kProposeChunk) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        // compact the chunk's free agents of proposing species into s_list
+#pragma unroll
+        for (int u = 0; u < kProposeChunk / kThreads; u++) {
+            const uint32_t i = base + u * kThreads + threadIdx.x;
+            bool isp = false;
+            if (i < n) {
+                const uint32_t meta = (uint32_t)pm[i].w;
+                if (!(meta & M_BOUND)) {
+                    const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+                    isp = B.models[S.model].sp[meta & M_SP].partner_mask != 0ull;
+                }
             }
-        claim(B, best, ida, gi);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isp);
+            uint32_t pos = 0;
+            if (lane == 0 && bal) pos = atomicAdd(&s_n, (uint32_t)__popc(bal));
+            pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+            if (isp) s_list[pos + __popc(bal & ((1u << lane) - 1u))] = i;
+        }
+        __syncthreads();
+        const uint32_t np = s_n;
+        for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
+            const uint32_t gi = s_list[k];
+            const int4 p = pm[gi];
+            const uint32_t meta = (uint32_t)p.w;
+            const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+            const ModelDev& Mo = B.models[S.model];
+            const uint32_t sp = meta & M_SP;
+            const uint64_t mask = Mo.sp[sp].partner_mask;
+            const int rmax = Mo.sp[sp].rmax;
+            const int g = (int)S.g, sh = (int)S.shift;
+            const int xlo = max((p.x - rmax) >> sh, 0), xhi = min((p.x + rmax) >> sh, g - 1);
+            const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
+            const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
+            Best best;
+            uint32_t ida = kNone;
+            for (int zz = zlo; zz <= zhi; zz++)
+                for (int yy = ylo; yy <= yhi; yy++) {
+                    const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
+                    const uint32_t j1 = start[row + xhi + 1];
+                    for (uint32_t j = start[row + xlo]; j < j1; j++)
+                        if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
+                }
+            claim(B, best, ida, gi);
+        }
+        __syncthreads();
     }
 }
 
