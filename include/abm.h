@@ -188,6 +188,26 @@ abm_status  abm_batch_live_agents(abm_batch* b, uint64_t* out);  /* syncs */
 const char* abm_batch_last_error(const abm_batch* b);
 void        abm_batch_destroy(abm_batch* b);  /* NULL-safe */
 
+/* ---------------- dump without allocation ---------------- */
+/* The same id-sorted records as abm_dump, for callers that cannot allocate
+ * device memory at the time of the call: abm_dump allocates a device staging
+ * buffer per call (cudaMalloc, which also synchronises the device), which a
+ * per-step monitor hook with a time budget, or a host application whose own
+ * allocator owns all device memory, cannot allow.  This call allocates
+ * nothing: records are staged in a fixed device array of 131,072 records
+ * (3 MiB) that every GPU loading the library holds until exit, then copied
+ * into `out` (host, cap records) and sorted there in place.  The paper has no
+ * counterpart; it is a property of this library only.
+ *  - out == NULL: returns the record count in *n_out (a size query).
+ *  - More than 131,072 records: ABM_ECAPACITY, with the limit named in
+ *    abm_last_error; the handle stays usable (use abm_dump instead).
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the array (each clears its counter first); calls that
+ *    overlap on the GPU race.  Synchronous. */
+abm_status  abm_dump_noalloc(abm_sim* sim, abm_record* out, size_t cap, size_t* n_out);
+
 /* ---------------- profiling ---------------- */
 /* Runs n steps without the CUDA graph, with a CUDA event on the stream
  * before and after each of the step's kernels, and writes the summed time of

@@ -10,7 +10,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["kernels.cu", "api.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
 HEADERS = ["engine.cuh", os.path.join("..", "..", "include", "abm.h")]
 OUT = os.path.join(HERE, "libabm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

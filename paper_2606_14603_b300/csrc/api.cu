@@ -926,3 +926,18 @@ abm_status abm_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Internal view of a simulation handle for the library's other translation
+// units (no effect on any state).
+namespace abm {
+bool internal_view(abm_sim* s, Buffers* B, Launch* L, cudaStream_t* stream, int32_t* sim, std::string** err) {
+    if (!s || !s->b || s->b->failed) return false;
+    *B = s->b->B;
+    *L = s->b->L;
+    *stream = s->b->stream;
+    *sim = s->id;
+    *err = &s->b->err;
+    return true;
+}
+}  // namespace abm
