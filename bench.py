@@ -39,7 +39,8 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["cascade", "nuclear", "toy"], default="cascade")
+    p.add_argument("--workload", choices=["cascade", "nuclear", "toy", "sweep"], default="cascade")
+    p.add_argument("--sweep-steps", type=int, default=50, help="steps per sim in the sweep summary")
     p.add_argument("--agents", type=int, default=0, help="override the agent count")
     p.add_argument("--profile-steps", type=int, default=50)
     p.add_argument("--no-flush", action="store_true", help="do not flush L2 between steps")
@@ -200,6 +201,49 @@ def cpu_baseline(model, seed, name, seconds=12.0):
             "sample": f"{name}: the first {steps} steps from t = 0, serial oracle, one thread"}
 
 
+def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0):
+    """The 64-sim dose x seed sweep: all sims stepped together in one batch
+    versus each sim alone, one after the other (same library, same step count,
+    CUDA-graph replay in both, no L2 flush: the batch's 12.6M-agent state
+    exceeds L2 while the small sims alone fit in it)."""
+    import workloads as W
+    sims = W.sweep(scale)
+    models = [m for m, _ in sims]
+    n_total = sum(m.n_agents for m in models)
+    cap, cells = A.batch_capacity(models)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b = A.Batch(cap, cells, len(sims), stream=stream)
+    ids = [b.add(m, s) for m, s in sims]
+    b.step(warmup)
+    b.sync()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.sync()
+    batched_ms = e0.elapsed_time(e1)
+    live = sum(molecules(b.counts(i), m) for i, m in zip(ids, models))
+    b.close()
+    serial_ms = 0.0
+    for m, s in sims:
+        sim = A.Sim(m, s, stream=stream)
+        sim.step(warmup)
+        sim.sync()
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        serial_ms += e0.elapsed_time(e1)
+        sim.close()
+    batched = n_total * steps / (batched_ms / 1e3)
+    serial = n_total * steps / (serial_ms / 1e3)
+    return {"sims": len(sims), "agents": n_total, "live_after": live, "steps": steps,
+            "batched_value": batched, "serial_value": serial, "unit": UNIT,
+            "batched_over_serial": batched / serial, "batched_ms_per_step": batched_ms / steps,
+            "serial_ms_per_round": serial_ms / steps}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -221,6 +265,21 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if args.workload == "sweep":
+        stream = torch.cuda.Stream()
+        with Clocks(local) as clk:
+            sw = run_sweep(A, torch, stream, args.steps, args.warmup)
+        line = {"metric": METRIC, "value": sw["batched_value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": sw["batched_ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": "sweep_64_sims_50k_500k", "agents": sw["agents"],
+                           "l2": "no flush (batched state 12.6M agents exceeds L2)"},
+                "sweep": sw, "gpu_launches": A.N_STEP_KERNELS * args.steps, "clocks": clk.summary()}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     model, seed, name = workload(args)
     seed = seed + rank                      # independent replicas
@@ -323,6 +382,10 @@ def main():
                "steps": Ke, "includes": "abm_create (model upload, device-side placement) + per step "
                                        "abm_step + abm_counts read back to host"}
 
+    sweep = None
+    if args.sweep_steps > 0 and args.workload == "cascade" and not args.agents:
+        sweep = run_sweep(A, torch, stream, args.sweep_steps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(model, seed, name)
@@ -336,7 +399,7 @@ def main():
             "p50_step_ms": per_step[len(per_step) // 2], "p99_step_ms": per_step[int(0.99 * (len(per_step) - 1))],
             "roofline": roof, "step_roofline": step_roof,
             "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
-            "gpu_launches": A.N_STEP_KERNELS * K, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": A.N_STEP_KERNELS * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
             "clocks": clocks, "wall_s_timed_region": wall}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -153,6 +153,12 @@ typedef struct abm_sim abm_sim;
 size_t      abm_arena_bytes(const abm_model* model, const abm_options* opt);
 abm_status  abm_create(const abm_model* model, uint64_t seed, const abm_options* opt,
                        abm_sim** out);
+/* Grid of a model (host only, no device work): the cell edge 2^(*shift_out)
+ * units chosen for cell_log2 (0 = automatic: about one agent per cell at the
+ * initial density, never below the largest contact radius) and the number of
+ * cells, for sizing a batch's capacity_cells.  ABM_EINVAL for invalid input. */
+abm_status  abm_model_grid(const abm_model* model, uint32_t cell_log2, uint32_t* shift_out,
+                           uint64_t* cells_out);
 abm_status  abm_step(abm_sim* sim, uint32_t n);
 abm_status  abm_counts(abm_sim* sim, uint64_t* out, size_t cap, size_t* n_out);
 abm_status  abm_digest(abm_sim* sim, uint64_t* out);

@@ -108,6 +108,7 @@ def lib():
             "abm_batch_profile_step": (C.c_int, [P, C.c_uint32, P, C.c_uint32]),
             "abm_kernel_name": (C.c_char_p, [C.c_uint32]),
             "abm_grid_cells": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+            "abm_model_grid": (C.c_int, [C.POINTER(Model), C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -163,6 +164,24 @@ def arena_bytes(model, capacity: int = 0, cell_log2: int = 0, births_per_step: i
     ms = _ModelStructs(model)
     o = Options(capacity, cell_log2, births_per_step, None, 0, None, None)
     return lib().abm_arena_bytes(C.byref(ms.model), C.byref(o))
+
+
+def model_grid(model, cell_log2: int = 0):
+    """(cell_log2, cells) of a model's grid, without touching the device."""
+    ms = _ModelStructs(model)
+    sh, cells = C.c_uint32(), C.c_uint64()
+    _check(lib().abm_model_grid(C.byref(ms.model), cell_log2, C.byref(sh), C.byref(cells)))
+    return sh.value, cells.value
+
+
+def batch_capacity(models, headroom: float = 1.25, cell_log2_delta: int = 0):
+    """(capacity_agents, capacity_cells) for a batch of these models."""
+    agents = sum(m.n_agents for m in models)
+    cells = 0
+    for m in models:
+        sh, _ = model_grid(m)
+        cells += model_grid(m, max(1, sh + cell_log2_delta))[1] if cell_log2_delta else model_grid(m)[1]
+    return int(agents * headroom) + 65536, cells
 
 
 class Sim:

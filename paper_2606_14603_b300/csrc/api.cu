@@ -828,6 +828,25 @@ size_t abm_arena_bytes(const abm_model* model, const abm_options* opt) {
     return bytes;
 }
 
+abm_status abm_model_grid(const abm_model* model, uint32_t cell_log2, uint32_t* shift_out, uint64_t* cells_out) {
+    if (!shift_out || !cells_out) return ABM_EINVAL;
+    Compiled* c = new (std::nothrow) Compiled();
+    if (!c) return ABM_ENOMEM;
+    std::string msg;
+    abm_status st = compile_model(model, c, &msg);
+    if (st == ABM_OK) {
+        const uint32_t shift = cell_log2 ? cell_log2 : auto_shift(*c);
+        if (shift > 30 || (1ll << shift) < c->Rmax) {
+            st = ABM_EINVAL;
+        } else {
+            *shift_out = shift;
+            *cells_out = cells_for(*c, shift);
+        }
+    }
+    delete c;
+    return st;
+}
+
 abm_status abm_create(const abm_model* model, uint64_t seed, const abm_options* opt, abm_sim** out) {
     if (!out) return ABM_EINVAL;
     *out = nullptr;
