@@ -39,7 +39,9 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["cascade", "nuclear", "toy", "sweep"], default="cascade")
+    p.add_argument("--workload", choices=["cascade", "nuclear", "toy", "sweep", "serve"], default="cascade")
+    p.add_argument("--serve-seconds", type=float, default=20.0,
+                   help="seconds of job arrivals in the serving measurement (the served config runs 600)")
     p.add_argument("--sweep-steps", type=int, default=50, help="steps per sim in the sweep summary")
     p.add_argument("--agents", type=int, default=0, help="override the agent count")
     p.add_argument("--profile-steps", type=int, default=50)
@@ -64,7 +66,8 @@ def config_of(args, model, name, extra=None):
     c = {"workload": name, "agents": model.n_agents, "species": len(model.species),
          "reactions": len(model.reactions), "compartments": len(model.compartments),
          "dt_s": model.dt_s, "position_unit_nm": model.unit_nm,
-         "l2": "no flush" if args.no_flush else "flushed between timed steps (256 MB write)"}
+         "l2": "no flush" if args.no_flush else
+               "flushed between timed steps: 256 MB write, then a 256 MB read (cold, clean L2)"}
     if extra:
         c.update(extra)
     return c
@@ -244,6 +247,24 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0):
             "serial_ms_per_round": serial_ms / steps}
 
 
+def run_serve(A, seconds, budget=150e9):
+    """Served workload: Poisson arrivals (20/s, seed 7) of cascade or
+    two-compartment jobs, 10k-2M agents, 1k-20k steps, admitted under an HBM
+    budget, continuous batching; runs `seconds` of arrivals in real time and
+    reports the jobs that completed within that window."""
+    import workloads as W
+    from paper_2606_14603_b300 import serve
+    jobs = W.served_jobs(duration_s=seconds)
+    srv = serve.Server(budget_bytes=budget)
+    out = serve.run(jobs, srv, duration_s=seconds, real_time=True, drain=False)
+    srv.close()
+    out.pop("results")
+    out["arrival_rate_per_s"] = 20.0
+    out["budget_bytes"] = budget
+    out["window_s"] = seconds
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -266,6 +287,19 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    if args.workload == "serve":
+        with Clocks(local) as clk:
+            sv = run_serve(A, args.serve_seconds)
+        line = {"metric": METRIC, "value": sv["throughput_molecule_steps_per_s"], "unit": UNIT, "n_gpus": world,
+                "steps": sv["steps_run"], "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "served_poisson_20_per_s", "window_s": args.serve_seconds,
+                           "budget_gb": 150},
+                "serve": sv, "clocks": clk.summary()}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+
     if args.workload == "sweep":
         stream = torch.cuda.Stream()
         with Clocks(local) as clk:
@@ -286,6 +320,15 @@ def main():
     stream = torch.cuda.Stream()
     sim = A.Sim(model, seed, stream=stream)
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_src = None if args.no_flush else torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        # write 256 MB (evicts the simulation state from the 126 MB L2), then
+        # read 256 MB so that the flush's own dirty lines are written back here
+        # and not inside the next timed step
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            flush_src.sum()
 
     # warm-up (untimed)
     sim.step(args.warmup)
@@ -302,8 +345,7 @@ def main():
         wall0 = time.perf_counter()
         for k in range(K):
             if flush is not None:
-                with torch.cuda.stream(stream):
-                    flush.zero_()
+                flush_l2()
             starts[k].record(stream)
             sim.step(1)
             ends[k].record(stream)
@@ -332,8 +374,7 @@ def main():
     P = max(1, args.profile_steps)
     for _ in range(P):
         if flush is not None:
-            with torch.cuda.stream(stream):
-                flush.zero_()
+            flush_l2()
         for k, v in sim.profile_step(1).items():
             prof[k] += v
     tot = sum(prof.values())
@@ -386,6 +427,12 @@ def main():
     if args.sweep_steps > 0 and args.workload == "cascade" and not args.agents:
         sweep = run_sweep(A, torch, stream, args.sweep_steps)
 
+    served = None
+    if args.serve_seconds > 0 and args.workload == "cascade" and not args.agents:
+        sim.close()
+        served = run_serve(A, args.serve_seconds)
+        sim = None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(model, seed, name)
@@ -400,10 +447,12 @@ def main():
             "roofline": roof, "step_roofline": step_roof,
             "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
             "gpu_launches": A.N_STEP_KERNELS * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
+            "serve": served,
             "clocks": clocks, "wall_s_timed_region": wall}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if dist:
         dist.destroy_process_group()
 

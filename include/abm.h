@@ -180,6 +180,11 @@ abm_status  abm_batch_create(const abm_batch_options* opt, abm_batch** out);
  * Synchronises the stream.  ABM_ECAPACITY if agents, cells or slots run out. */
 abm_status  abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed,
                           uint32_t cell_log2, int32_t* sim_id);
+/* Freeze a simulation once its step counter reaches max_step (absolute):
+ * later steps keep its agents in place without advancing them, so a server
+ * can step a batch in fixed epochs and still read every simulation at its
+ * exact last step.  0xFFFFFFFF (the default) never freezes.  Synchronises. */
+abm_status  abm_batch_set_max_step(abm_batch* b, int32_t sim_id, uint32_t max_step);
 /* Retire a simulation: its agents are dropped by the next step's grid build
  * and its slot, agents and cells become free for later admissions. */
 abm_status  abm_batch_remove(abm_batch* b, int32_t sim_id);

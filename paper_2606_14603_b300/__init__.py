@@ -93,6 +93,7 @@ def lib():
             "abm_batch_create": (C.c_int, [C.POINTER(BatchOptions), C.POINTER(P)]),
             "abm_batch_add": (C.c_int, [P, C.POINTER(Model), C.c_uint64, C.c_uint32, C.POINTER(C.c_int32)]),
             "abm_batch_remove": (C.c_int, [P, C.c_int32]),
+            "abm_batch_set_max_step": (C.c_int, [P, C.c_int32, C.c_uint32]),
             "abm_batch_step": (C.c_int, [P, C.c_uint32]),
             "abm_batch_counts": (C.c_int, [P, C.c_int32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_batch_digest": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
@@ -303,6 +304,10 @@ class Batch:
                lib().abm_batch_last_error, self._h)
         self._n_counts[sid.value] = ms.n_counts
         return sid.value
+
+    def set_max_step(self, sim: int, max_step: int) -> None:
+        """Freeze `sim` once its step counter reaches max_step."""
+        _check(lib().abm_batch_set_max_step(self._h, sim, max_step), lib().abm_batch_last_error, self._h)
 
     def remove(self, sim: int) -> None:
         _check(lib().abm_batch_remove(self._h, sim), lib().abm_batch_last_error, self._h)

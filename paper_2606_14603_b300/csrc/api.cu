@@ -287,6 +287,7 @@ struct abm_batch {
     std::vector<HostSim> sims;
     std::vector<uint32_t> cell_off_host;  // persistent sources of async copies
     uint32_t n_cells_host = 0;
+    uint32_t max_step_host = 0;
     std::vector<ModelDev> model_host;   // copies of the uploaded model tables
     std::vector<int> model_refs;
     uint32_t n_sims_used = 0;
@@ -414,6 +415,26 @@ uint64_t cells_in_use(const abm_batch* b) {
     for (uint32_t s = 0; s < b->n_sims_used; s++)
         if (b->sims[s].state == 1) off += b->sims[s].n_cells;
     return off;
+}
+
+// Drop the agents of retired simulations (between steps) and free their slots.
+abm_status compact(abm_batch* b, Ctl* h) {
+    const uint32_t zero = 0;
+    CU(cudaMemcpyAsync(&b->B.ctl->n_sorted, &zero, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(launch_compact(b->B, b->L, b->stream));
+    uint32_t kept = 0;
+    CU(cudaMemcpyAsync(&kept, &b->B.ctl->n_sorted, 4, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    const uint32_t nxt = h->cur ^ 1u;
+    CU(cudaMemcpyAsync(&b->B.ctl->cur, &nxt, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemcpyAsync(&b->B.ctl->n_in, &kept, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemsetAsync(&b->B.ctl->n_sorted, 0, 4, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    for (auto& s : b->sims)
+        if (s.state == 2) s.state = 0;
+    h->cur = nxt;
+    h->n_in = kept;
+    return ABM_OK;
 }
 
 }  // namespace
@@ -596,6 +617,18 @@ abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, ui
         return st;
     }
     if ((uint64_t)h.n_in + c->n0 > b->cap_agents) {
+        // agents of retired sims still occupy slots until the next step: drop them now
+        bool draining = false;
+        for (uint32_t s = 0; s < b->max_sims; s++) draining |= b->sims[s].state == 2;
+        if (draining) {
+            st = compact(b, &h);
+            if (st != ABM_OK) {
+                delete c;
+                return st;
+            }
+        }
+    }
+    if ((uint64_t)h.n_in + c->n0 > b->cap_agents) {
         b->err = "agent capacity exhausted";
         delete c;
         return ABM_ECAPACITY;
@@ -633,6 +666,7 @@ abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, ui
     sd.g = (uint32_t)((c->geo.ext >> shift) + 1);
     sd.n_counts = c->dev.n_counts;
     sd.counts_off = (uint32_t)slot * 512u;
+    sd.max_step = 0xFFFFFFFFu;
     auto& hs = b->sims[slot];
     hs.state = 1;
     hs.model_slot = (uint32_t)mslot;
@@ -665,6 +699,16 @@ abm_status abm_batch_remove(abm_batch* b, int32_t sim) {
     b->sims[sim].state = 2;
     b->model_refs[b->sims[sim].model_slot]--;
     return repack_cells(b);
+}
+
+abm_status abm_batch_set_max_step(abm_batch* b, int32_t sim, uint32_t max_step) {
+    if (!b) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    b->max_step_host = max_step;
+    CU(cudaMemcpyAsync(&b->B.sims[sim].max_step, &b->max_step_host, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return ABM_OK;
 }
 
 abm_status abm_batch_step(abm_batch* b, uint32_t n) {

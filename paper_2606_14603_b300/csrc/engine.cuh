@@ -96,7 +96,8 @@ struct SimDev {              // per simulation slot
     uint32_t cell_off;       // first global cell
     uint32_t n_counts;       // counts vector length
     uint32_t counts_off;     // offset into the counts buffer
-    uint32_t pad[3];
+    uint32_t max_step;       // the sim is frozen (kept, not advanced) once step reaches this
+    uint32_t pad[2];
 };
 
 struct Ctl {
@@ -238,6 +239,8 @@ cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, in
 // The step with a CUDA event before and after each of its kernels (ev[0..5]).
 constexpr int kStepKernels = 5;
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev);
+// Between steps: drop the agents of retired simulations (counter: ctl.n_sorted).
+cudaError_t launch_compact(const Buffers& B, const Launch& L, cudaStream_t s);
 cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim, void* d_out,
                         uint32_t cap);
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,

@@ -84,6 +84,146 @@ __device__ __forceinline__ void brownian_move(const SimDev& S, const SpeciesDev&
 // k_move: P1 first-order events and P2 move for every agent of the current
 // buffer, then the cell key and the agent's rank inside its cell (the value
 // returned by the histogram atomic), which the scatter uses directly.
+// Work of one agent of the move pass, split into phases so that a thread can
+// keep the memory round trips of several agents in flight at once.
+struct MoveState {
+    int4 p;              // record, moved in place
+    uint32_t id;
+    uint32_t flags;      // 1 alive, 2 emit, 4 moves (M > 0)
+    const SimDev* S;
+    const ModelDev* Mo;
+    uint32_t mw;         // crossing draw
+    int32_t z[3];        // Gaussian table entries (loads in flight between phases)
+    uint32_t key;
+};
+
+// Phase 1: P1 events (a released partner is moved and placed right away:
+// rare) and the move draw; issues the three table loads.
+__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, uint32_t par, MoveState& a) {
+    uint32_t meta = (uint32_t)a.p.w;
+    a.flags = 0;
+    if (meta & (M_DEAD | M_ABSORBED)) return;
+    const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+    if (!S.active) return;
+    const ModelDev& Mo = B.models[S.model];
+    a.S = &S;
+    a.Mo = &Mo;
+    const uint32_t t = S.step;
+    if (t >= S.max_step) {  // frozen: kept in place, not advanced
+        a.flags = 1u;
+        return;
+    }
+    bool alive = true, emit = false;
+    if (meta & M_BOUND) {
+        const uint4 e = philox(make_uint4(a.id, t, 1u, 0u), S.key0, S.key1);
+        const ReactionDev& R = Mo.rx[(meta & M_RXN) >> M_RXN_SHIFT];
+        if ((uint64_t)e.x < R.thr_rel) {
+            const bool ra = meta & M_ROLE_A;
+            const int cprod = ra ? R.prod_a : R.prod_b;
+            const int hprod = ra ? R.prod_b : R.prod_a;
+            meta &= ~(M_BOUND | M_ROLE_A | M_RXN);
+            if (hprod >= 0) {  // the partner reappears here and moves on its own
+                int4 q = a.p;
+                q.w = (int)((meta & ~M_SP) | (uint32_t)hprod);
+                brownian_move(S, Mo.sp[hprod], B.ztab, q, par, t);
+                const uint32_t k = reserve(&ctl->n_extra);
+                if (k < B.cap_extras) {
+                    const uint32_t key = cell_of(S, q.x, q.y, q.z);
+                    const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
+                    B.xpm[k] = q;
+                    B.xid[k] = par;
+                    B.xkr[k] = (uint64_t)key << 32 | rank;
+                } else {
+                    raise_error(ctl, ERR_CAPACITY_EXTRAS, k);
+                }
+            }
+            if (cprod >= 0) meta = (meta & ~M_SP) | (uint32_t)cprod;
+            else alive = false;
+        }
+    } else {
+        const SpeciesDev& sd = Mo.sp[meta & M_SP];
+        if (sd.has_event) {
+            const uint4 e = philox(make_uint4(a.id, t, 1u, 0u), S.key0, S.key1);
+            if ((uint64_t)e.y < sd.thr_uni) {
+                if (sd.uni_to >= 0) meta = (meta & ~M_SP) | (uint32_t)sd.uni_to;
+                else alive = false;
+            } else if ((uint64_t)e.z < sd.thr_emit) {
+                emit = true;
+            }
+        }
+    }
+    a.p.w = (int)meta;
+    if (!alive) return;
+    a.flags = 1u | (emit ? 2u : 0u);
+    if (Mo.sp[meta & M_SP].M) {
+        const uint4 m = philox(make_uint4(a.id, t, 0u, 0u), S.key0, S.key1);
+        a.z[0] = __ldg(&B.ztab[m.x >> 16]);
+        a.z[1] = __ldg(&B.ztab[m.y >> 16]);
+        a.z[2] = __ldg(&B.ztab[m.z >> 16]);
+        a.mw = m.w;
+        a.flags |= 4u;
+    }
+}
+
+// Phase 2: apply the step (walls, membranes) and compute the cell key.
+__device__ __forceinline__ void move_phase2(MoveState& a) {
+    if (!(a.flags & 1u)) return;
+    const SimDev& S = *a.S;
+    if (a.flags & 4u) {
+        const SpeciesDev& sd = a.Mo->sp[(uint32_t)a.p.w & M_SP];
+        int32_t x = a.p.x + gauss_step(a.z[0], sd.M);
+        int32_t y = a.p.y + gauss_step(a.z[1], sd.M);
+        int32_t z = a.p.z + gauss_step(a.z[2], sd.M);
+        if (!S.root_sphere) {
+            x = fold(x, S.ext);
+            y = fold(y, S.ext);
+            z = fold(z, S.ext);
+        }
+        const int c = locate(S, x, y, z);
+        bool accept = c >= 0;  // outside the spherical cell: rejected
+        if (accept) {
+            const uint32_t comp = ((uint32_t)a.p.w & M_COMP) >> M_COMP_SHIFT;
+            if ((uint32_t)c != comp) {
+                if ((uint64_t)a.mw >= sd.thr_cross) accept = false;  // membrane: rejected
+                else a.p.w = (int)(((uint32_t)a.p.w & ~M_COMP) | ((uint32_t)c << M_COMP_SHIFT));
+            }
+        }
+        if (accept) {
+            a.p.x = x;
+            a.p.y = y;
+            a.p.z = z;
+        }
+    }
+    a.key = cell_of(S, a.p.x, a.p.y, a.p.z);
+}
+
+// Phase 4: results (the histogram rank comes from phase 3) and births.
+__device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, const MoveState& a,
+                                            uint32_t rank) {
+    if (!(a.flags & 1u)) {
+        B.kr[i] = kInvalidKey;
+        return;
+    }
+    B.kr[i] = (uint64_t)a.key << 32 | rank;
+    B.pm[cur][i] = a.p;
+    if (a.flags & 2u) {
+        const uint32_t meta = (uint32_t)a.p.w;
+        const uint32_t k = reserve(&ctl->n_births);
+        if (k < B.cap_births) {
+            const uint32_t child = (uint32_t)a.Mo->sp[meta & M_SP].emit;
+            B.bpm[k] = make_int4(a.p.x, a.p.y, a.p.z, (int)((meta & ~(M_SP | M_RXN | M_BOUND | M_ROLE_A)) | child));
+            B.bpar[k] = a.id;
+        } else {
+            raise_error(ctl, ERR_CAPACITY_BIRTHS, k);
+        }
+    }
+}
+
+#ifndef ABM_MOVE_ILP
+#define ABM_MOVE_ILP 1
+#endif
+constexpr int kMoveILP = ABM_MOVE_ILP;
+
 __global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
@@ -93,94 +233,39 @@ __global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
         ctl->scan_ticket = 0;
         ctl->n_sorted = 0;  // the scan's last tile writes the real count
     }
-    int4* __restrict__ pm = B.pm[cur];
+    const int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
     const uint32_t* __restrict__ apar = B.apar[cur];
     // proposal slots touched last step become empty again (the list is short)
     const uint32_t np = ctl->n_props;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x)
-        B.acc[B.props[k].y] = kEmpty;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int4 p = pm[i];
-        uint32_t meta = (uint32_t)p.w;
-        if (meta & (M_DEAD | M_ABSORBED)) {
-            B.kr[i] = kInvalidKey;
-            continue;
-        }
-        const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
-        if (!S.active) {
-            B.kr[i] = kInvalidKey;
-            continue;
-        }
-        const ModelDev& Mo = B.models[S.model];
-        const uint32_t id = aid[i];
-        const uint32_t t = S.step;
-        bool alive = true, emit = false, released = false;
-        int4 q = p;
-        uint32_t qid = 0;
-        if (meta & M_BOUND) {
-            const uint4 e = philox(make_uint4(id, t, 1u, 0u), S.key0, S.key1);
-            const ReactionDev& R = Mo.rx[(meta & M_RXN) >> M_RXN_SHIFT];
-            if ((uint64_t)e.x < R.thr_rel) {
-                const bool ra = meta & M_ROLE_A;
-                const int cprod = ra ? R.prod_a : R.prod_b;
-                const int hprod = ra ? R.prod_b : R.prod_a;
-                meta &= ~(M_BOUND | M_ROLE_A | M_RXN);
-                if (hprod >= 0) {
-                    released = true;
-                    qid = apar[i];
-                    q.w = (int)((meta & ~M_SP) | (uint32_t)hprod);
-                }
-                if (cprod >= 0) meta = (meta & ~M_SP) | (uint32_t)cprod;
-                else alive = false;
-            }
-        } else {
-            const SpeciesDev& sd = Mo.sp[meta & M_SP];
-            if (sd.has_event) {
-                const uint4 e = philox(make_uint4(id, t, 1u, 0u), S.key0, S.key1);
-                if ((uint64_t)e.y < sd.thr_uni) {
-                    if (sd.uni_to >= 0) meta = (meta & ~M_SP) | (uint32_t)sd.uni_to;
-                    else alive = false;
-                } else if ((uint64_t)e.z < sd.thr_emit) {
-                    emit = true;
-                }
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
+    // kMoveILP agents per thread, phase by phase, so that their loads, table
+    // lookups and histogram atomics overlap
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kMoveILP * stride) {
+        MoveState a[kMoveILP];
+        uint32_t par[kMoveILP];
+#pragma unroll
+        for (int u = 0; u < kMoveILP; u++) {
+            const uint32_t i = i0 + u * stride;
+            a[u].flags = 0;
+            if (i < n) {
+                a[u].p = pm[i];
+                a[u].id = aid[i];
+                par[u] = apar[i];
             }
         }
-        if (alive) {
-            p.w = (int)meta;
-            brownian_move(S, Mo.sp[meta & M_SP], B.ztab, p, id, t);
-            meta = (uint32_t)p.w;  // compartment after the move
-            const uint32_t key = cell_of(S, p.x, p.y, p.z);
-            const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
-            B.kr[i] = (uint64_t)key << 32 | rank;
-            pm[i] = p;
-        } else {
-            B.kr[i] = kInvalidKey;
-        }
-        if (emit) {
-            const uint32_t k = reserve(&ctl->n_births);
-            if (k < B.cap_births) {
-                const uint32_t child = (uint32_t)Mo.sp[meta & M_SP].emit;
-                B.bpm[k] = make_int4(p.x, p.y, p.z,
-                                     (int)((meta & ~(M_SP | M_RXN | M_BOUND | M_ROLE_A)) | child));
-                B.bpar[k] = id;
-            } else {
-                raise_error(ctl, ERR_CAPACITY_BIRTHS, k);
-            }
-        }
-        if (released) {
-            brownian_move(S, Mo.sp[(uint32_t)q.w & M_SP], B.ztab, q, qid, t);
-            const uint32_t k = reserve(&ctl->n_extra);
-            if (k < B.cap_extras) {
-                const uint32_t key = cell_of(S, q.x, q.y, q.z);
-                const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
-                B.xpm[k] = q;
-                B.xid[k] = qid;
-                B.xkr[k] = (uint64_t)key << 32 | rank;
-            } else {
-                raise_error(ctl, ERR_CAPACITY_EXTRAS, k);
-            }
-        }
+#pragma unroll
+        for (int u = 0; u < kMoveILP; u++)
+            if (i0 + u * stride < n) move_phase1(B, ctl, i0 + u * stride, par[u], a[u]);
+#pragma unroll
+        for (int u = 0; u < kMoveILP; u++) move_phase2(a[u]);
+        uint32_t rank[kMoveILP];
+#pragma unroll
+        for (int u = 0; u < kMoveILP; u++) rank[u] = (a[u].flags & 1u) ? atomicAdd(&B.cnt[a[u].key], 1u) : 0u;
+#pragma unroll
+        for (int u = 0; u < kMoveILP; u++)
+            if (i0 + u * stride < n) move_phase4(B, ctl, cur, i0 + u * stride, a[u], rank[u]);
     }
 }
 
@@ -430,7 +515,7 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
                 const uint32_t meta = (uint32_t)pm[i].w;
                 if (!(meta & M_BOUND)) {
                     const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
-                    isp = B.models[S.model].sp[meta & M_SP].partner_mask != 0ull;
+                    isp = S.step < S.max_step && B.models[S.model].sp[meta & M_SP].partner_mask != 0ull;
                 }
             }
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isp);
@@ -533,7 +618,7 @@ __device__ void finalize_block(Buffers& B) {
     }
     const uint32_t n_sims = ctl->n_sims;
     for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
-        if (B.sims[s].active) B.sims[s].step += 1;
+        if (B.sims[s].active && B.sims[s].step < B.sims[s].max_step) B.sims[s].step += 1;
     __syncthreads();
     if (threadIdx.x == 0) {
         ctl->n_in = ns + nb;
@@ -708,6 +793,24 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
     }
 }
 
+// k_compact: between steps, copy the agents of active simulations (dropping
+// those of retired ones) to the other buffer; storage order is free.
+__global__ void __launch_bounds__(kThreads) k_compact(Buffers B) {
+    Ctl* ctl = B.ctl;
+    const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
+    const uint32_t n = ctl->n_in;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 p = B.pm[cur][i];
+        const uint32_t meta = (uint32_t)p.w;
+        if (meta & (M_DEAD | M_ABSORBED)) continue;
+        if (!B.sims[meta >> M_SIM_SHIFT].active) continue;
+        const uint32_t k = reserve(&ctl->n_sorted);
+        B.pm[nxt][k] = p;
+        B.aid[nxt][k] = B.aid[cur][i];
+        if (meta & M_BOUND) B.apar[nxt][k] = B.apar[cur][i];
+    }
+}
+
 // k_dump: one record per agent of `sim` (two for a complex), unordered.
 __global__ void __launch_bounds__(kThreads) k_dump(Buffers B, int32_t sim, uint4* out_lo, uint2* out_hi,
                                                    uint32_t cap) {
@@ -787,6 +890,11 @@ cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint3
 
 cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest) {
     k_observe<<<L.blocks_agents, kThreads, 0, s>>>(B, only_sim, want_digest);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Buffers& B, const Launch& L, cudaStream_t s) {
+    k_compact<<<L.blocks_agents, kThreads, 0, s>>>(B);
     return cudaGetLastError();
 }
 

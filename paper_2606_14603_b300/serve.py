@@ -1,0 +1,213 @@
+"""Continuous-batching server for simulation jobs on one GPU.
+
+Jobs (a model, a seed, a step count) arrive over time.  The server keeps one
+batch whose arena is sized from an HBM budget; between epochs it admits every
+arrived job that fits (agent slots, grid cells, simulation slots), steps all
+resident jobs together for an epoch, and retires the jobs that reached their
+step count, reading their counts and digest first.  A job's latency runs from
+its arrival to the moment its result is back on the host.
+
+The engine's arithmetic does not depend on what else is in the batch, so every
+job's result is bit-identical to the same job run alone (tests check this).
+
+This is host-side orchestration over the C ABI: admission, retirement and
+epoch sizing happen here, every step runs in the engine's kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+from . import Batch, model_grid
+
+# bytes of one agent slot and one grid cell in the batch arena (see the
+# layout in csrc/api.cu); used only to turn an HBM budget into capacities
+BYTES_PER_AGENT_SLOT = 100
+BYTES_PER_CELL = 12
+
+
+@dataclasses.dataclass
+class JobResult:
+    job_id: int
+    arrival_s: float
+    admitted_s: float
+    finished_s: float
+    steps: int
+    agents: int
+    counts: np.ndarray
+    digest: int
+
+    @property
+    def latency_s(self) -> float:
+        return self.finished_s - self.arrival_s
+
+
+@dataclasses.dataclass
+class _Resident:
+    job: object
+    sid: int
+    remaining: int
+    admitted_s: float
+    agents: int
+    cells: int
+
+
+class Server:
+    """Continuous batching of simulation jobs under an HBM budget.
+
+    budget_bytes: device memory for the shared arena (agents and cells split
+    by `cells_per_agent`, unless capacities are given); max_sims: concurrent
+    jobs; epoch: steps between admission points.  A job is frozen on the
+    device at its own last step, so epochs need not stop at job boundaries."""
+
+    def __init__(self, budget_bytes: float = 150e9, max_sims: int = 256, epoch: int = 50,
+                 cells_per_agent: float = 1.3, headroom: float = 1.25, stream=None,
+                 capacity_agents: Optional[int] = None, capacity_cells: Optional[int] = None):
+        per_agent = BYTES_PER_AGENT_SLOT + cells_per_agent * BYTES_PER_CELL
+        cap_agents = capacity_agents or min(int(budget_bytes / per_agent), 2_000_000_000)
+        cap_cells = capacity_cells or min(int(cap_agents * cells_per_agent), 4_000_000_000)
+        self.cap_agents, self.cap_cells = cap_agents, cap_cells
+        self.max_sims = max_sims
+        self.epoch = epoch
+        self.headroom = headroom
+        self.batch = Batch(cap_agents, cap_cells, max_sims, stream=stream)
+        self.resident: Dict[int, _Resident] = {}
+        self.used_agents = 0
+        self.used_cells = 0
+        self.steps_run = 0
+        self.molecule_steps = 0
+        self.max_resident = 0
+        self.waited = 0          # admissions that had to wait for capacity
+
+    # -- capacity accounting (reserved per job: initial agents x headroom) --
+    def need(self, job):
+        return int(job.model.n_agents * self.headroom) + 1, model_grid(job.model)[1]
+
+    def can_ever_fit(self, job) -> bool:
+        a, c = self.need(job)
+        return a <= self.cap_agents and c <= self.cap_cells
+
+    def fits(self, job) -> bool:
+        need_a, need_c = self.need(job)
+        return (len(self.resident) < self.max_sims and self.used_agents + need_a <= self.cap_agents
+                and self.used_cells + need_c <= self.cap_cells)
+
+    def admit(self, job, now: float) -> None:
+        need_a, need_c = self.need(job)
+        sid = self.batch.add(job.model, job.seed)
+        self.batch.set_max_step(sid, job.steps)
+        self.resident[sid] = _Resident(job, sid, job.steps, now, need_a, need_c)
+        self.used_agents += need_a
+        self.used_cells += need_c
+        self.max_resident = max(self.max_resident, len(self.resident))
+
+    def step_epoch(self) -> int:
+        """Step the batch for one epoch (at most the largest remaining count);
+        jobs that reach their own last step inside it are frozen there."""
+        if not self.resident:
+            return 0
+        k = min(max(r.remaining for r in self.resident.values()), self.epoch)
+        self.batch.step(k)
+        for r in self.resident.values():
+            done = min(k, r.remaining)
+            r.remaining -= done
+            self.molecule_steps += r.job.model.n_agents * done
+        self.steps_run += k
+        return k
+
+    def retire_finished(self, clock: Callable[[], float]) -> List[JobResult]:
+        done = []
+        for sid in [s for s, r in self.resident.items() if r.remaining == 0]:
+            r = self.resident.pop(sid)
+            counts = self.batch.counts(sid)
+            digest = self.batch.digest(sid)
+            now = clock()
+            self.batch.remove(sid)
+            self.used_agents -= r.agents
+            self.used_cells -= r.cells
+            done.append(JobResult(r.job.job_id, r.job.arrival_s, r.admitted_s, now, r.job.steps,
+                                  r.job.model.n_agents, counts, digest))
+        return done
+
+    def close(self) -> None:
+        self.batch.close()
+
+
+def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: bool = True,
+        drain: bool = True) -> dict:
+    """Serve `jobs` (sorted by arrival_s) and return throughput and latency
+    statistics.  With real_time the arrivals follow the wall clock; otherwise
+    a job arrives as soon as the server looks for new work after its arrival
+    time on a virtual clock that only advances with the GPU work done."""
+    pending = list(jobs)
+    pending.sort(key=lambda j: j.arrival_s)
+    queue: List = []                    # arrived, not admitted (FIFO by arrival)
+    results: List[JobResult] = []
+    rejected: List[int] = []
+    waited = set()
+    t0 = time.perf_counter()
+    virtual = [0.0]
+
+    def clock() -> float:
+        if real_time:
+            return time.perf_counter() - t0
+        return virtual[0]
+
+    i = 0
+    horizon = duration_s if duration_s is not None else math.inf
+    while True:
+        now = clock()
+        while i < len(pending) and pending[i].arrival_s <= now and pending[i].arrival_s < horizon:
+            if server.can_ever_fit(pending[i]):
+                queue.append(pending[i])
+            else:
+                rejected.append(pending[i].job_id)
+            i += 1
+        # admit in arrival order while they fit (no overtaking)
+        if queue and not server.fits(queue[0]) and queue[0].job_id not in waited:
+            waited.add(queue[0].job_id)
+            server.waited += 1
+        while queue and server.fits(queue[0]):
+            server.admit(queue.pop(0), clock())
+        if server.resident:
+            w0 = time.perf_counter()
+            server.step_epoch()
+            if not real_time:
+                server.batch.sync()     # the virtual clock advances by GPU time
+            results += server.retire_finished(clock)
+            if not real_time:
+                virtual[0] += time.perf_counter() - w0
+        else:
+            if i >= len(pending) or pending[i].arrival_s >= horizon:
+                if not queue:
+                    break
+            elif real_time:
+                time.sleep(max(0.0, min(pending[i].arrival_s - clock(), 0.01)))
+            else:
+                virtual[0] = max(virtual[0], pending[i].arrival_s)
+        if not drain and clock() >= horizon:
+            break
+    wall = clock()
+    lat = np.array([r.latency_s for r in results]) if results else np.zeros(0)
+    offered = sum(j.model.n_agents * j.steps for j in pending if j.arrival_s < horizon)
+    return {
+        "jobs_offered": sum(1 for j in pending if j.arrival_s < horizon),
+        "jobs_completed": len(results),
+        "wall_s": wall,
+        "throughput_molecule_steps_per_s": server.molecule_steps / wall if wall > 0 else 0.0,
+        "completed_molecule_steps_per_s": sum(r.agents * r.steps for r in results) / wall if wall > 0 else 0.0,
+        "jobs_per_s": len(results) / wall if wall > 0 else 0.0,
+        "offered_molecule_steps_per_s": offered / horizon if math.isfinite(horizon) and horizon > 0 else None,
+        "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+        "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+        "latency_max_s": float(lat.max()) if len(lat) else None,
+        "jobs_rejected": len(rejected),
+        "steps_run": server.steps_run,
+        "max_resident": server.max_resident,
+        "admissions_waited": server.waited,
+        "results": results,
+    }

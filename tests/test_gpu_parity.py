@@ -240,3 +240,24 @@ def test_capacity_overflow_is_reported(A):
         g.counts()
     assert e.value.status == A.ECAPACITY
     g.close()
+
+
+def test_admission_right_after_removal_compacts(A, oracle_mod):
+    """Capacity is only enough once the retired sim's agents are dropped:
+    the admission compacts the arrays without stepping anything."""
+    m1, m2, m3 = W.mapk(9_000), W.mapk(6_000, drug_frac=0.0), W.toy(900, 800, edge_um=0.5)
+    cells = sum(A.model_grid(m)[1] for m in (m1, m2, m3))
+    b = A.Batch(16_000, cells, 3)
+    s1 = b.add(m1, 1)
+    s2 = b.add(m2, 2)
+    b.step(17)
+    b.remove(s1)
+    s3 = b.add(m3, 3)                      # 6k + 1.7k live, 9k retired: needs compaction
+    b.step(23)
+    o2 = oracle_mod.OracleSim(m2, 2)
+    o2.step(40)
+    o3 = oracle_mod.OracleSim(m3, 3)
+    o3.step(23)
+    assert b.digest(s2) == o2.digest()
+    assert b.digest(s3) == o3.digest()
+    b.close()

@@ -1,0 +1,61 @@
+"""Serving: continuous batching of jobs that arrive over time (GPU).
+
+Jobs arrive while others are resident; they are admitted as memory and slots
+free up and are stepped together.  Every job's result (counts and digest at
+its last step) must equal the same job run alone, bit for bit."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_common import engine, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    specs = [
+        (0.000, W.mapk(20_000), 5, 120),
+        (0.001, W.nuclear(15_000, boost=100.0, n_genes=16, genes_on=8), 6, 200),
+        (0.002, W.mapk(12_000, drug_frac=0.0), 7, 60),
+        (0.050, W.toy(800, 700, edge_um=0.5), 8, 150),
+        (0.060, W.mapk(30_000, drug_frac=0.05), 9, 90),
+        (0.200, W.nuclear(9_000, boost=50.0, n_genes=8, genes_on=4), 10, 70),
+        (0.210, W.mapk(8_000), 11, 40),
+    ]
+    return [W.Job(k, t, m, s, n) for k, (t, m, s, n) in enumerate(specs)]
+
+
+def test_served_jobs_equal_alone_runs():
+    require_gpu()
+    A = engine()
+    from paper_2606_14603_b300 import serve
+    jobs = _jobs()
+    # small capacities: not all jobs fit at once, so admission has to wait
+    caps = [A.model_grid(j.model)[1] for j in jobs]
+    srv = serve.Server(capacity_agents=45_000, capacity_cells=2 * max(caps), max_sims=3, epoch=25)
+    out = serve.run(jobs, srv, real_time=False)
+    srv.close()
+    assert out["jobs_completed"] == len(jobs) and out["jobs_rejected"] == 0
+    assert out["max_resident"] >= 2                       # work overlapped on the device
+    assert out["admissions_waited"] >= 1                  # admission by the budget
+    by_id = {r.job_id: r for r in out["results"]}
+    for j in jobs:
+        alone = A.Sim(j.model, j.seed)
+        alone.step(j.steps)
+        r = by_id[j.job_id]
+        assert r.digest == alone.digest(), f"job {j.job_id}"
+        assert np.array_equal(r.counts, alone.counts()), f"job {j.job_id}"
+        alone.close()
+    lat = [r.latency_s for r in out["results"]]
+    assert out["latency_p50_s"] <= out["latency_p99_s"] and min(lat) >= 0
+
+
+def test_server_rejects_jobs_that_can_never_fit():
+    require_gpu()
+    engine()
+    from paper_2606_14603_b300 import serve
+    jobs = [W.Job(0, 0.0, W.mapk(200_000), 1, 10), W.Job(1, 0.0, W.mapk(5_000), 2, 10)]
+    srv = serve.Server(capacity_agents=20_000, capacity_cells=10_000_000, max_sims=2)
+    out = serve.run(jobs, srv, real_time=False)
+    srv.close()
+    assert out["jobs_rejected"] == 1 and out["jobs_completed"] == 1
