@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-flush", action="store_true", help="do not flush L2 between steps")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ref-seconds", type=float, default=90.0, help="oracle time budget of --impl reference")
     return p.parse_args()
 
 
@@ -160,6 +161,18 @@ def ncu_traffic(kernel):
 
 
 # ---------------------------------------------------------------------------
+def reduce_over_ranks(total_ms, molecule_steps, device="cuda"):
+    """Whole-job numbers over all ranks: the slowest rank's timed total and
+    the sum of the molecule-steps every rank processed."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, molecule_steps], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def run_reference(args, rank):
     """The oracle on the host cores, on a bounded sample of the same workload."""
     import oracle
@@ -168,8 +181,8 @@ def run_reference(args, rank):
     t0 = time.perf_counter()
     sim.step(1)
     est = time.perf_counter() - t0
-    budget = 90.0
-    warm = min(args.warmup, max(0, int(10.0 / max(est, 1e-6))))
+    budget = args.ref_seconds
+    warm = min(args.warmup, max(0, int(0.1 * budget / max(est, 1e-6))))
     sim.step(warm)
     steps = max(1, min(args.steps, int(budget / max(est, 1e-6))))
     n0 = molecules(sim.counts(), model)
@@ -359,11 +372,7 @@ def main():
     n_after = molecules(sim.counts(), model)
     mol_steps = 0.5 * (n_before + n_after) * K
     if dist:
-        t = torch.tensor([total_ms, mol_steps], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, mol_steps_all = float(tmax[0]), float(t[1])
+        total_ms_max, mol_steps_all = reduce_over_ranks(total_ms, mol_steps)
     else:
         total_ms_max, mol_steps_all = total_ms, mol_steps
     value = mol_steps_all / (total_ms_max / 1e3)
