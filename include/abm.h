@@ -123,7 +123,7 @@ typedef struct {
 typedef struct {
     uint64_t       capacity_agents;  /* slots shared by all sims (> 0)     */
     uint64_t       capacity_cells;   /* grid cells shared by all sims      */
-    uint32_t       max_sims;         /* 1..4096                            */
+    uint32_t       max_sims;         /* 1..2048                            */
     uint32_t       births_per_step;  /* 0 = 8192 (also the maximum)        */
     void*          arena;
     size_t         arena_bytes;

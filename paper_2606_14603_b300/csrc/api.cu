@@ -239,7 +239,7 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
     const size_t sizes[] = {
         16 * C, 16 * C,                        // pm[2]
         4 * C, 4 * C, 4 * C, 4 * C,            // aid[2], apar[2]
-        8 * C, 8 * C, 8 * C,                   // kr, acc, props
+        8 * C, 8 * C, 8 * C, (size_t)C,        // kr, acc, props, pflag
         16 * E, 4 * E, 8 * E,                  // extras
         16 * (size_t)Bc, 4 * (size_t)Bc,       // births
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
@@ -509,6 +509,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.kr = (uint64_t*)at();
     B.acc = (uint64_t*)at();
     B.props = (uint2*)at();
+    B.pflag = (uint8_t*)at();
     B.xpm = (int4*)at();
     B.xid = (uint32_t*)at();
     B.xkr = (uint64_t*)at();

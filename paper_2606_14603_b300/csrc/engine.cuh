@@ -7,6 +7,7 @@
 //   kr[C]        u64 (cell << 32 | rank within cell) from the move pass
 //   acc[C]       u64 proposal slot, min of (dist^2 << 32 | proposer id)
 //   props[C]     (proposer, target) sorted indices of this step's proposals
+//   pflag[C]     1 if the sorted agent is a free proposer (written by the scatter)
 //   xpm/xid/xkr  released partners appended by the move pass (C/2 + 1)
 //   bpm/bpar     births of the step (B)
 //   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
@@ -15,7 +16,8 @@
 //
 // meta word: bits 0-5 species, 6-7 compartment, 8 carrier, 9 carrier is
 // reactant a, 10 dead, 11 absorbed (became hidden this step), 12-19 reaction
-// of the complex, 20-31 simulation slot.
+// of the complex, 20-30 simulation slot, 31 the species proposes (kept in
+// step with every change of species).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -25,7 +27,7 @@ namespace abm {
 constexpr int kMaxSpecies = 64;
 constexpr int kMaxReactions = 255;
 constexpr int kMaxComp = 4;
-constexpr int kMaxSims = 4096;
+constexpr int kMaxSims = 2048;
 constexpr uint32_t kMaxBirths = 8192;
 constexpr int kScanTile = 8192;           // cells per scan tile (256 threads x 32)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -39,7 +41,8 @@ constexpr uint32_t M_ROLE_A = 1u << 9;
 constexpr uint32_t M_DEAD = 1u << 10;
 constexpr uint32_t M_ABSORBED = 1u << 11;
 constexpr uint32_t M_RXN_SHIFT = 12, M_RXN = 0xFFu << 12;
-constexpr uint32_t M_SIM_SHIFT = 20;
+constexpr uint32_t M_SIM_SHIFT = 20, M_SIM_MASK = 0x7FFu;
+constexpr uint32_t M_PROP = 1u << 31;       // free agent of a species that proposes
 
 // device error codes (ctl.err); mapped to abm_status on the host
 enum : uint32_t {
@@ -126,6 +129,7 @@ struct Buffers {
     uint64_t* kr;
     uint64_t* acc;
     uint2* props;
+    uint8_t* pflag;
     int4* xpm;
     uint32_t* xid;
     uint64_t* xkr;
@@ -157,9 +161,9 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u;  // one 32x32->64 product each
+        const uint64_t p1 = (uint64_t)c.z * 0xCD9E8D57u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
     }
     return c;
 }
@@ -216,6 +220,14 @@ __device__ __forceinline__ uint64_t record_hash(uint32_t id, uint32_t sp, uint32
     h = fmix64(h ^ ((uint64_t)(uint32_t)x | (uint64_t)(uint32_t)y << 32));
     h = fmix64(h ^ ((uint64_t)(uint32_t)z | (uint64_t)partner << 32));
     return h;
+}
+
+__host__ __device__ __forceinline__ uint32_t sim_of(uint32_t meta) { return (meta >> M_SIM_SHIFT) & M_SIM_MASK; }
+
+// meta with species sp, the proposer bit following the species
+__device__ __forceinline__ uint32_t with_species(uint32_t meta, uint32_t sp, const ModelDev& Mo) {
+    meta = (meta & ~(M_SP | M_PROP)) | sp;
+    return Mo.sp[sp].partner_mask ? meta | M_PROP : meta;
 }
 
 __device__ __forceinline__ void raise_error(Ctl* ctl, uint32_t code, uint32_t info) {

@@ -103,7 +103,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, ui
     uint32_t meta = (uint32_t)a.p.w;
     a.flags = 0;
     if (meta & (M_DEAD | M_ABSORBED)) return;
-    const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+    const SimDev& S = B.sims[sim_of(meta)];
     if (!S.active) return;
     const ModelDev& Mo = B.models[S.model];
     a.S = &S;
@@ -124,7 +124,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, ui
             meta &= ~(M_BOUND | M_ROLE_A | M_RXN);
             if (hprod >= 0) {  // the partner reappears here and moves on its own
                 int4 q = a.p;
-                q.w = (int)((meta & ~M_SP) | (uint32_t)hprod);
+                q.w = (int)with_species(meta, (uint32_t)hprod, Mo);
                 brownian_move(S, Mo.sp[hprod], B.ztab, q, par, t);
                 const uint32_t k = reserve(&ctl->n_extra);
                 if (k < B.cap_extras) {
@@ -137,7 +137,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, ui
                     raise_error(ctl, ERR_CAPACITY_EXTRAS, k);
                 }
             }
-            if (cprod >= 0) meta = (meta & ~M_SP) | (uint32_t)cprod;
+            if (cprod >= 0) meta = with_species(meta, (uint32_t)cprod, Mo);
             else alive = false;
         }
     } else {
@@ -145,7 +145,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, ui
         if (sd.has_event) {
             const uint4 e = philox(make_uint4(a.id, t, 1u, 0u), S.key0, S.key1);
             if ((uint64_t)e.y < sd.thr_uni) {
-                if (sd.uni_to >= 0) meta = (meta & ~M_SP) | (uint32_t)sd.uni_to;
+                if (sd.uni_to >= 0) meta = with_species(meta, (uint32_t)sd.uni_to, Mo);
                 else alive = false;
             } else if ((uint64_t)e.z < sd.thr_emit) {
                 emit = true;
@@ -211,7 +211,8 @@ __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, 
         const uint32_t k = reserve(&ctl->n_births);
         if (k < B.cap_births) {
             const uint32_t child = (uint32_t)a.Mo->sp[meta & M_SP].emit;
-            B.bpm[k] = make_int4(a.p.x, a.p.y, a.p.z, (int)((meta & ~(M_SP | M_RXN | M_BOUND | M_ROLE_A)) | child));
+            B.bpm[k] = make_int4(a.p.x, a.p.y, a.p.z,
+                                 (int)with_species(meta & ~(M_RXN | M_BOUND | M_ROLE_A), child, *a.Mo));
             B.bpar[k] = a.id;
         } else {
             raise_error(ctl, ERR_CAPACITY_BIRTHS, k);
@@ -434,9 +435,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
                 raise_error(ctl, ERR_CAPACITY_AGENTS, dest[u]);
                 continue;
             }
+            const uint32_t meta = (uint32_t)p[u].w;
             B.pm[nxt][dest[u]] = p[u];
             B.aid[nxt][dest[u]] = id[u];
-            if ((uint32_t)p[u].w & M_BOUND) B.apar[nxt][dest[u]] = par[u];
+            B.pflag[dest[u]] = (meta & (M_PROP | M_BOUND)) == M_PROP;
+            if (meta & M_BOUND) B.apar[nxt][dest[u]] = par[u];
         }
     }
 }
@@ -510,14 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
 #pragma unroll
         for (int u = 0; u < kProposeChunk / kThreads; u++) {
             const uint32_t i = base + u * kThreads + threadIdx.x;
-            bool isp = false;
-            if (i < n) {
-                const uint32_t meta = (uint32_t)pm[i].w;
-                if (!(meta & M_BOUND)) {
-                    const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
-                    isp = S.step < S.max_step && B.models[S.model].sp[meta & M_SP].partner_mask != 0ull;
-                }
-            }
+            const bool isp = i < n && B.pflag[i];
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isp);
             uint32_t pos = 0;
             if (lane == 0 && bal) pos = atomicAdd(&s_n, (uint32_t)__popc(bal));
@@ -530,7 +526,8 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
             const uint32_t gi = s_list[k];
             const int4 p = pm[gi];
             const uint32_t meta = (uint32_t)p.w;
-            const SimDev& S = B.sims[meta >> M_SIM_SHIFT];
+            const SimDev& S = B.sims[sim_of(meta)];
+            if (S.step >= S.max_step) continue;  // frozen simulation
             const ModelDev& Mo = B.models[S.model];
             const uint32_t sp = meta & M_SP;
             const uint64_t mask = Mo.sp[sp].partner_mask;
@@ -574,7 +571,7 @@ __device__ void finalize_block(Buffers& B) {
     }
     // key of birth k: simulation in the high word, parent id in the low word
     auto key_of = [&](uint32_t k) -> uint64_t {
-        return (uint64_t)((uint32_t)B.bpm[k].w >> M_SIM_SHIFT) << 32 | B.bpar[k];
+        return (uint64_t)(sim_of((uint32_t)B.bpm[k].w)) << 32 | B.bpar[k];
     };
     // rank of each birth among the births of its simulation (ids are unique:
     // at most one birth per parent per step), and whether it is the last one
@@ -652,13 +649,13 @@ __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
         uint32_t* wa = reinterpret_cast<uint32_t*>(&pm[i]) + 3;
         uint32_t* wb = reinterpret_cast<uint32_t*>(&pm[j]) + 3;
         uint32_t ma = *wa, mb = *wb;
-        const SimDev& S = B.sims[ma >> M_SIM_SHIFT];
+        const SimDev& S = B.sims[sim_of(ma)];
         const ModelDev& Mo = B.models[S.model];
         const uint32_t r = Mo.rx_of[ma & M_SP][mb & M_SP];
         const ReactionDev& R = Mo.rx[r];
         if (R.kind == 0) {  // CONVERT
-            ma = R.prod_a >= 0 ? (ma & ~M_SP) | (uint32_t)R.prod_a : ma | M_DEAD;
-            mb = R.prod_b >= 0 ? (mb & ~M_SP) | (uint32_t)R.prod_b : mb | M_DEAD;
+            ma = R.prod_a >= 0 ? with_species(ma, (uint32_t)R.prod_a, Mo) : ma | M_DEAD;
+            mb = R.prod_b >= 0 ? with_species(mb, (uint32_t)R.prod_b, Mo) : mb | M_DEAD;
         } else if (R.carrier_a) {  // BIND, a carries b
             ma |= M_BOUND | M_ROLE_A | (r << M_RXN_SHIFT);
             apar[i] = aid[j];
@@ -707,7 +704,8 @@ __global__ void __launch_bounds__(kThreads) k_init(Buffers B, uint32_t sim, uint
             placed = locate(S, x, y, z) == want;
         }
         if (!placed) raise_error(ctl, ERR_PLACEMENT, k);
-        B.pm[cur][base + k] = make_int4(x, y, z, (int)((sim << M_SIM_SHIFT) | ((uint32_t)want << M_COMP_SHIFT) | sp));
+        const uint32_t meta = with_species((sim << M_SIM_SHIFT) | ((uint32_t)want << M_COMP_SHIFT), sp, Mo);
+        B.pm[cur][base + k] = make_int4(x, y, z, (int)meta);
         B.aid[cur][base + k] = k;
     }
 }
@@ -732,7 +730,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
     if (threadIdx.x == 0) {
         uint32_t s0 = kNone;
         if (only_sim >= 0) s0 = (uint32_t)only_sim;
-        else if (begin < end) s0 = (uint32_t)B.pm[cur][begin].w >> M_SIM_SHIFT;
+        else if (begin < end) s0 = sim_of((uint32_t)B.pm[cur][begin].w);
         s_sim = s0;
     }
     __syncthreads();
@@ -741,7 +739,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
         const int4 p = B.pm[cur][i];
         const uint32_t meta = (uint32_t)p.w;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
-        const uint32_t s = meta >> M_SIM_SHIFT;
+        const uint32_t s = sim_of(meta);
         if (only_sim >= 0 && s != (uint32_t)only_sim) continue;
         const SimDev& S = B.sims[s];
         if (!S.active) continue;
@@ -803,7 +801,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(Buffers B) {
         const int4 p = B.pm[cur][i];
         const uint32_t meta = (uint32_t)p.w;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
-        if (!B.sims[meta >> M_SIM_SHIFT].active) continue;
+        if (!B.sims[sim_of(meta)].active) continue;
         const uint32_t k = reserve(&ctl->n_sorted);
         B.pm[nxt][k] = p;
         B.aid[nxt][k] = B.aid[cur][i];
@@ -823,7 +821,7 @@ __global__ void __launch_bounds__(kThreads) k_dump(Buffers B, int32_t sim, uint4
         const int4 p = B.pm[cur][i];
         const uint32_t meta = (uint32_t)p.w;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
-        if ((meta >> M_SIM_SHIFT) != (uint32_t)sim) continue;
+        if (sim_of(meta) != (uint32_t)sim) continue;
         const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
         const uint32_t id = B.aid[cur][i];
         const bool bound = meta & M_BOUND;

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_dump_static(Buffers B, int32_t sim, Dum
         const int4 p = B.pm[cur][i];
         const uint32_t meta = (uint32_t)p.w;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
-        if ((meta >> M_SIM_SHIFT) != (uint32_t)sim) continue;
+        if (sim_of(meta) != (uint32_t)sim) continue;
         const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
         const uint32_t id = B.aid[cur][i];
         const bool bound = meta & M_BOUND;
