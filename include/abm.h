@@ -159,6 +159,17 @@ abm_status  abm_create(const abm_model* model, uint64_t seed, const abm_options*
  * cells, for sizing a batch's capacity_cells.  ABM_EINVAL for invalid input. */
 abm_status  abm_model_grid(const abm_model* model, uint32_t cell_log2, uint32_t* shift_out,
                            uint64_t* cells_out);
+/* Resume a simulation from a checkpoint: the model and seed it was created
+ * with, the records abm_dump returned (any order), and its step counter
+ * (abm_step_index) and next id (last entry of abm_counts) at the time of the
+ * dump.  All randomness is keyed by (seed, step, id), so continuing the
+ * restored simulation reproduces the original trajectory bit for bit.
+ * Records are checked (ids unique and below next_id, places inside the
+ * domain and in their compartment, complexes complete): ABM_EINVAL
+ * otherwise.  The model's initial counts are ignored. */
+abm_status  abm_restore(const abm_model* model, uint64_t seed, const abm_options* opt,
+                        const abm_record* records, size_t n_records, uint32_t step,
+                        uint32_t next_id, abm_sim** out);
 abm_status  abm_step(abm_sim* sim, uint32_t n);
 abm_status  abm_counts(abm_sim* sim, uint64_t* out, size_t cap, size_t* n_out);
 abm_status  abm_digest(abm_sim* sim, uint64_t* out);
@@ -180,6 +191,10 @@ abm_status  abm_batch_create(const abm_batch_options* opt, abm_batch** out);
  * Synchronises the stream.  ABM_ECAPACITY if agents, cells or slots run out. */
 abm_status  abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed,
                           uint32_t cell_log2, int32_t* sim_id);
+/* abm_restore into a batch slot (synchronises, like abm_batch_add). */
+abm_status  abm_batch_restore(abm_batch* b, const abm_model* model, uint64_t seed,
+                              uint32_t cell_log2, const abm_record* records, size_t n_records,
+                              uint32_t step, uint32_t next_id, int32_t* sim_id);
 /* Freeze a simulation once its step counter reaches max_step (absolute):
  * later steps keep its agents in place without advancing them, so a server
  * can step a batch in fixed epochs and still read every simulation at its

@@ -81,6 +81,10 @@ def lib():
         sig = {
             "abm_arena_bytes": (C.c_size_t, [C.POINTER(Model), C.POINTER(Options)]),
             "abm_create": (C.c_int, [C.POINTER(Model), C.c_uint64, C.POINTER(Options), C.POINTER(P)]),
+            "abm_restore": (C.c_int, [C.POINTER(Model), C.c_uint64, C.POINTER(Options), P, C.c_size_t,
+                                      C.c_uint32, C.c_uint32, C.POINTER(P)]),
+            "abm_batch_restore": (C.c_int, [P, C.POINTER(Model), C.c_uint64, C.c_uint32, P, C.c_size_t,
+                                            C.c_uint32, C.c_uint32, C.POINTER(C.c_int32)]),
             "abm_step": (C.c_int, [P, C.c_uint32]),
             "abm_counts": (C.c_int, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_digest": (C.c_int, [P, C.POINTER(C.c_uint64)]),
@@ -191,7 +195,9 @@ class Sim:
     torch.cuda.Stream or a raw cudaStream_t."""
 
     def __init__(self, model, seed: int, capacity: int = 0, cell_log2: int = 0,
-                 births_per_step: int = 0, arena=None, stream=None, ncdf_table=None):
+                 births_per_step: int = 0, arena=None, stream=None, ncdf_table=None, restore=None):
+        """restore=(records, step, next_id) resumes from a checkpoint (see
+        checkpoint()) instead of placing the model's initial agents."""
         L = lib()
         ms = _ModelStructs(model)
         self.n_counts = ms.n_counts
@@ -206,9 +212,15 @@ class Sim:
             aptr, abytes = arena.data_ptr(), arena.numel() * arena.element_size()
         o = Options(capacity, cell_log2, births_per_step, aptr, abytes, _stream_ptr(stream), tptr)
         h = C.c_void_p()
-        st = L.abm_create(C.byref(ms.model), seed, C.byref(o), C.byref(h))
+        if restore is None:
+            st = L.abm_create(C.byref(ms.model), seed, C.byref(o), C.byref(h))
+        else:
+            rec, step, next_id = restore
+            rec = np.ascontiguousarray(rec, dtype=RECORD_DTYPE)
+            st = L.abm_restore(C.byref(ms.model), seed, C.byref(o), rec.ctypes.data if len(rec) else None,
+                               len(rec), step, next_id, C.byref(h))
         if st != OK:
-            raise AbmError(st, "abm_create failed")
+            raise AbmError(st, "abm_create failed" if restore is None else "abm_restore failed")
         self._h = h
 
     def step(self, n: int = 1) -> None:
@@ -235,6 +247,10 @@ class Sim:
         m = C.c_size_t()
         _check(lib().abm_dump(self._h, out.ctypes.data, out.size, C.byref(m)), lib().abm_last_error, self._h)
         return out[: m.value]
+
+    def checkpoint(self):
+        """(records, step, next_id): everything needed to resume this simulation."""
+        return self.dump(), self.t, int(self.counts()[-1])
 
     def profile_step(self, n: int = 1) -> dict:
         """n un-graphed steps with CUDA events around each kernel: ms per kernel."""

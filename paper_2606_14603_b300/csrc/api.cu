@@ -579,7 +579,89 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
         if (e_ != cudaSuccess) return cuda_fail(b, e_, #call); \
     } while (0)
 
-abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, uint32_t cell_log2, int32_t* sim_id) {
+// Agents of a restored simulation, in the engine's layout (hidden partners
+// travel inside their carriers' records).
+struct RestoreSet {
+    std::vector<int4> pm;
+    std::vector<uint32_t> id, par;
+    uint32_t step = 0, next_id = 0;
+};
+
+// Convert and check abm_dump records against a compiled model: ids unique
+// and below next_id, species/compartment/reaction in range, positions inside
+// the domain and in their compartment, every carrier's hidden partner
+// present with the matching reaction.
+static abm_status restore_set(const Compiled& c, const abm_record* rec, size_t n, uint32_t step,
+                              uint32_t next_id, RestoreSet* out, std::string* err) {
+    out->step = step;
+    out->next_id = next_id;
+    std::vector<const abm_record*> sorted(n);
+    for (size_t i = 0; i < n; i++) sorted[i] = rec + i;
+    std::sort(sorted.begin(), sorted.end(), [](const abm_record* a, const abm_record* b) { return a->id < b->id; });
+    auto bad = [&](const char* m) {
+        *err = m;
+        return ABM_EINVAL;
+    };
+    const SimDev& g = c.geo;
+    auto find = [&](uint32_t id) -> const abm_record* {
+        auto it = std::lower_bound(sorted.begin(), sorted.end(), id,
+                                   [](const abm_record* r, uint32_t v) { return r->id < v; });
+        return it != sorted.end() && (*it)->id == id ? *it : nullptr;
+    };
+    for (size_t i = 0; i < n; i++) {
+        const abm_record& r = *sorted[i];
+        if (i && sorted[i - 1]->id == r.id) return bad("restore: duplicate agent id");
+        if (r.id >= next_id) return bad("restore: agent id not below next_id");
+        if (r.species >= c.dev.n_sp || r.compartment >= c.dev.n_comp) return bad("restore: species or compartment out of range");
+        if (r.x < 0 || r.y < 0 || r.z < 0 || r.x > g.ext || r.y > g.ext || r.z > g.ext) return bad("restore: position outside the domain");
+        if (r.flags & 2) continue;  // hidden: restored with its carrier
+        int64_t d = 0;
+        int comp = 0;
+        if (g.root_sphere) {
+            const int64_t dx = r.x - g.c0[0], dy = r.y - g.c0[1], dz = r.z - g.c0[2];
+            if (dx * dx + dy * dy + dz * dz > g.root_r2) return bad("restore: position outside the cell");
+        }
+        for (int k = 1; k < g.n_comp; k++) {
+            const int64_t dx = r.x - g.cc[k][0], dy = r.y - g.cc[k][1], dz = r.z - g.cc[k][2];
+            d = dx * dx + dy * dy + dz * dz;
+            if (d <= g.cr2[k]) {
+                comp = k;
+                break;
+            }
+        }
+        if (comp != r.compartment) return bad("restore: compartment does not match the position");
+        uint32_t meta = (uint32_t)r.compartment << M_COMP_SHIFT | r.species;
+        uint32_t par = kNone;
+        if (r.flags & 1) {
+            if (r.reaction >= c.dev.n_rx) return bad("restore: reaction out of range");
+            const ReactionDev& R = c.dev.rx[r.reaction];
+            const bool ra = r.flags & 4;
+            if (r.species != (ra ? R.a : R.b) || R.kind != ABM_BIND || (bool)R.carrier_a != ra)
+                return bad("restore: carrier does not match its reaction");
+            const abm_record* h = find(r.partner);
+            if (!h || !(h->flags & 2) || h->partner != r.id || h->reaction != r.reaction ||
+                h->species != (ra ? R.b : R.a))
+                return bad("restore: a carrier's hidden partner is missing or inconsistent");
+            meta |= M_BOUND | (ra ? M_ROLE_A : 0u) | (uint32_t)r.reaction << M_RXN_SHIFT;
+            par = r.partner;
+        } else if (c.dev.sp[r.species].partner_mask) {
+            meta |= M_PROP;
+        }
+        out->pm.push_back(make_int4(r.x, r.y, r.z, (int)meta));
+        out->id.push_back(r.id);
+        out->par.push_back(par);
+    }
+    for (size_t i = 0; i < n; i++) {  // every hidden record belongs to a carrier
+        const abm_record& r = *sorted[i];
+        if (!(r.flags & 2)) continue;
+        const abm_record* car = find(r.partner);
+        if (!car || !(car->flags & 1) || car->partner != r.id) return bad("restore: hidden agent without its carrier");
+    }
+    return ABM_OK;
+}
+
+static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, uint32_t cell_log2, bool restore,
+                          const abm_record* rec, size_t n_rec, uint32_t step, uint32_t next_id, int32_t* sim_id) {
     if (!b || !sim_id) return ABM_EINVAL;
     if (b->failed) return ABM_ESTATE;
     *sim_id = -1;
@@ -599,6 +681,16 @@ abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, ui
         return ABM_EINVAL;
     }
     const uint64_t ncell = cells_for(*c, shift);
+    RestoreSet rs;
+    if (restore) {
+        st = restore_set(*c, rec, n_rec, step, next_id, &rs, &msg);
+        if (st != ABM_OK) {
+            b->err = msg;
+            delete c;
+            return st;
+        }
+        c->n0 = rs.pm.size();  // agents to place
+    }
     // slot: a free one (draining slots become free after the next step)
     int32_t slot = -1;
     for (uint32_t s = 0; s < b->max_sims; s++)
@@ -661,8 +753,8 @@ abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, ui
     sd.model = (uint32_t)mslot;
     sd.key0 = (uint32_t)seed;
     sd.key1 = (uint32_t)(seed >> 32);
-    sd.step = 0;
-    sd.next_id = (uint32_t)c->n0;
+    sd.step = restore ? rs.step : 0;
+    sd.next_id = restore ? rs.next_id : (uint32_t)c->n0;
     sd.shift = shift;
     sd.g = (uint32_t)((c->geo.ext >> shift) + 1);
     sd.n_counts = c->dev.n_counts;
@@ -679,7 +771,17 @@ abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, ui
     CU(cudaMemcpyAsync(b->staging, c->species_end, 4 * kMaxSpecies, cudaMemcpyHostToDevice, b->stream));
     const uint32_t nsu = b->n_sims_used;
     CU(cudaMemcpyAsync(&b->B.ctl->n_sims, &nsu, 4, cudaMemcpyHostToDevice, b->stream));
-    CU(launch_init(b->B, b->L, b->stream, (uint32_t)slot, h.n_in, (uint32_t)c->n0, b->staging, c->dev.n_sp));
+    if (restore) {
+        for (auto& p : rs.pm) p.w |= (int)((uint32_t)slot << M_SIM_SHIFT);
+        const size_t k = rs.pm.size();
+        if (k) {
+            CU(cudaMemcpyAsync(b->B.pm[h.cur] + h.n_in, rs.pm.data(), 16 * k, cudaMemcpyHostToDevice, b->stream));
+            CU(cudaMemcpyAsync(b->B.aid[h.cur] + h.n_in, rs.id.data(), 4 * k, cudaMemcpyHostToDevice, b->stream));
+            CU(cudaMemcpyAsync(b->B.apar[h.cur] + h.n_in, rs.par.data(), 4 * k, cudaMemcpyHostToDevice, b->stream));
+        }
+    } else {
+        CU(launch_init(b->B, b->L, b->stream, (uint32_t)slot, h.n_in, (uint32_t)c->n0, b->staging, c->dev.n_sp));
+    }
     const uint32_t n_in = h.n_in + (uint32_t)c->n0;
     CU(cudaMemcpyAsync(&b->B.ctl->n_in, &n_in, 4, cudaMemcpyHostToDevice, b->stream));
     st = repack_cells(b);  // synchronises (host temporaries above stay alive until then)
@@ -689,6 +791,18 @@ abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, ui
     if (st != ABM_OK) return st;
     *sim_id = slot;
     return ABM_OK;
+}
+
+abm_status abm_batch_add(abm_batch* b, const abm_model* model, uint64_t seed, uint32_t cell_log2, int32_t* sim_id) {
+    return add_sim(b, model, seed, cell_log2, false, nullptr, 0, 0, 0, sim_id);
+}
+
+abm_status abm_batch_restore(abm_batch* b, const abm_model* model, uint64_t seed, uint32_t cell_log2,
+                             const abm_record* records, size_t n_records, uint32_t step, uint32_t next_id,
+                             int32_t* sim_id) {
+    if (!b || !sim_id || (n_records && !records)) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    return add_sim(b, model, seed, cell_log2, true, records, n_records, step, next_id, sim_id);
 }
 
 abm_status abm_batch_remove(abm_batch* b, int32_t sim) {
@@ -932,6 +1046,48 @@ abm_status abm_create(const abm_model* model, uint64_t seed, const abm_options* 
     s->b = b;
     s->id = id;
     *out = s;
+    return ABM_OK;
+}
+
+abm_status abm_restore(const abm_model* model, uint64_t seed, const abm_options* opt, const abm_record* records,
+                       size_t n_records, uint32_t step, uint32_t next_id, abm_sim** out) {
+    if (!out || (n_records && !records)) return ABM_EINVAL;
+    *out = nullptr;
+    Compiled* c = new (std::nothrow) Compiled();
+    if (!c) return ABM_ENOMEM;
+    std::string msg;
+    abm_status st = compile_model(model, c, &msg);
+    const uint32_t shift = st == ABM_OK ? (opt && opt->cell_log2 ? opt->cell_log2 : auto_shift(*c)) : 0;
+    const uint64_t cells = st == ABM_OK ? cells_for(*c, shift) : 0;
+    const bool small_cell = st == ABM_OK && (1ll << shift) < c->Rmax;
+    delete c;
+    if (st != ABM_OK || small_cell || shift > 30) return ABM_EINVAL;
+    abm_batch_options o{};
+    o.capacity_agents = opt && opt->capacity_agents ? opt->capacity_agents : n_records + n_records / 4 + 65536;
+    o.capacity_cells = cells;
+    o.max_sims = 1;
+    o.births_per_step = opt ? opt->births_per_step : 0;
+    o.arena = opt ? opt->arena : nullptr;
+    o.arena_bytes = opt ? opt->arena_bytes : 0;
+    o.stream = opt ? opt->stream : nullptr;
+    o.ncdf_table = opt ? opt->ncdf_table : nullptr;
+    abm_batch* b = nullptr;
+    st = abm_batch_create(&o, &b);
+    if (st != ABM_OK) return st;
+    int32_t id = -1;
+    st = abm_batch_restore(b, model, seed, shift, records, n_records, step, next_id, &id);
+    if (st != ABM_OK) {
+        abm_batch_destroy(b);
+        return st;
+    }
+    abm_sim* sim = new (std::nothrow) abm_sim();
+    if (!sim) {
+        abm_batch_destroy(b);
+        return ABM_ENOMEM;
+    }
+    sim->b = b;
+    sim->id = id;
+    *out = sim;
     return ABM_OK;
 }
 

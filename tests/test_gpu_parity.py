@@ -261,3 +261,47 @@ def test_admission_right_after_removal_compacts(A, oracle_mod):
     assert b.digest(s2) == o2.digest()
     assert b.digest(s3) == o3.digest()
     b.close()
+
+
+@pytest.mark.parametrize("which", ["mapk", "nuclear"])
+def test_checkpoint_restore_continues_bit_exact(A, oracle_mod, which):
+    if which == "mapk":
+        m, seed = W.mapk(25_000), 12
+    else:
+        m, seed = W.nuclear(20_000, boost=100.0, n_genes=16, genes_on=8), 42
+    g = A.Sim(m, seed)
+    g.step(60)
+    rec, t, next_id = g.checkpoint()
+    assert t == 60 and np.count_nonzero(rec["flags"] & 2) > 0
+    r = A.Sim(m, seed, restore=(rec[::-1].copy(), t, next_id))   # any record order
+    assert r.digest() == g.digest()
+    g.step(70)
+    r.step(70)
+    assert r.digest() == g.digest()
+    o = oracle_mod.OracleSim(m, seed)
+    o.step(130)
+    assert r.digest() == o.digest()
+    assert_same_dump(r.dump(), o.dump(), "restored at 130")
+    g.close()
+    r.close()
+
+
+def test_restore_rejects_inconsistent_records(A):
+    m = W.mapk(10_000)
+    g = A.Sim(m, 3)
+    g.step(40)
+    rec, t, next_id = g.checkpoint()
+    g.close()
+    bad = rec.copy()
+    bad["id"][1] = bad["id"][0]                           # duplicate id
+    with pytest.raises(A.AbmError):
+        A.Sim(m, 3, restore=(bad, t, next_id))
+    bad = rec.copy()
+    bad["x"][0] = -5                                      # outside the domain
+    with pytest.raises(A.AbmError):
+        A.Sim(m, 3, restore=(bad, t, next_id))
+    hid = np.nonzero(rec["flags"] & 2)[0]
+    if len(hid):
+        bad = np.delete(rec, hid[0])                      # a complex without its hidden partner
+        with pytest.raises(A.AbmError):
+            A.Sim(m, 3, restore=(bad, t, next_id))
