@@ -223,13 +223,13 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0):
     CUDA-graph replay in both, no L2 flush: the batch's 12.6M-agent state
     exceeds L2 while the small sims alone fit in it)."""
     import workloads as W
+    from paper_2606_14603_b300 import autotune
     sims = W.sweep(scale)
     models = [m for m, _ in sims]
     n_total = sum(m.n_agents for m in models)
-    cap, cells = A.batch_capacity(models)
+    best, tried = autotune.tune(sims, cell_deltas=(0, 1), blocks=(8, 16, 32), steps=10, warmup=2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    b = A.Batch(cap, cells, len(sims), stream=stream)
-    ids = [b.add(m, s) for m, s in sims]
+    b, ids = autotune.batch_for(sims, best.cell_delta, best.blocks_per_sm, stream=stream)
     b.step(warmup)
     b.sync()
     torch.cuda.synchronize()
@@ -255,6 +255,8 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0):
     batched = n_total * steps / (batched_ms / 1e3)
     serial = n_total * steps / (serial_ms / 1e3)
     return {"sims": len(sims), "agents": n_total, "live_after": live, "steps": steps,
+            "autotune": {"cell_delta": best.cell_delta, "blocks_per_sm": best.blocks_per_sm,
+                         "candidates": [[c.cell_delta, c.blocks_per_sm, round(c.ms_per_step, 4)] for c in tried]},
             "batched_value": batched, "serial_value": serial, "unit": UNIT,
             "batched_over_serial": batched / serial, "batched_ms_per_step": batched_ms / steps,
             "serial_ms_per_round": serial_ms / steps}

@@ -461,6 +461,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     if (!o || !o->capacity_agents || !o->capacity_cells || !o->max_sims || o->max_sims > (uint32_t)kMaxSims)
         return ABM_EINVAL;
     if (o->capacity_agents >= 0x7FFFFFFFull || o->capacity_cells >= 0xFFFFF000ull) return ABM_EINVAL;
+    if (o->blocks_per_sm > 64) return ABM_EINVAL;
     const uint32_t births = o->births_per_step ? o->births_per_step : kMaxBirths;
     if (births > kMaxBirths) return ABM_EINVAL;
     std::string msg;
@@ -540,7 +541,8 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t want = (b->cap_agents + 255) / 256;
     b->L.threads = 256;
-    b->L.blocks_agents = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 16));
+    const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : 16;
+    b->L.blocks_agents = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * per_sm));
     b->L.blocks_scan = (int)std::max<uint64_t>(1, std::min<uint64_t>(B.n_tiles_max, (uint64_t)sms * 4));
     b->L.blocks_accept = sms;
 

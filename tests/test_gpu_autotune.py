@@ -1,0 +1,28 @@
+"""Autotuner knobs do not change results (GPU): every (cell size, launch
+shape) candidate yields identical digests, equal to the oracle's."""
+import pytest
+
+import workloads as W
+from gpu_common import engine, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tuner_candidates_agree_and_match_oracle(oracle_mod):
+    require_gpu()
+    engine()
+    from paper_2606_14603_b300 import autotune
+    sims = [(W.mapk(9_000, drug_frac=0.03), 21), (W.nuclear(8_000, boost=50.0, n_genes=8, genes_on=4), 22),
+            (W.toy(700, 600, edge_um=0.45), 23)]
+    ref = []
+    for m, s in sims:
+        o = oracle_mod.OracleSim(m, s)
+        o.step(25)
+        ref.append(o.digest())
+    for d, bps in [(0, 0), (1, 4), (-1, 32), (2, 8)]:
+        b, ids = autotune.batch_for(sims, d, bps)
+        b.step(25)
+        assert [b.digest(i) for i in ids] == ref, (d, bps)
+        b.close()
+    best, allc = autotune.tune(sims, cell_deltas=(0, 1), blocks=(8, 16), steps=5, warmup=1)
+    assert len(allc) == 4 and best.ms_per_step == min(c.ms_per_step for c in allc)
