@@ -29,8 +29,8 @@ UNIT = "molecule-steps/s"
 # per-kernel bytes each launch must move per unit (agent or cell) in this
 # design; the step as a whole must read and rewrite the 20-byte agent record
 STEP_BYTES_PER_AGENT = 40
-KERNEL_BYTES = {"k_move": (44, "agent"), "k_scan": (12, "cell"), "k_scatter": (56, "agent"),
-                "k_propose": (24, "agent"), "k_accept": (4, "agent")}
+KERNEL_BYTES = {"k_move": (44, "agent"), "k_tiles": (4, "cell"), "k_scan": (12, "cell"),
+                "k_scatter": (56, "agent"), "k_propose": (24, "agent"), "k_accept": (4, "agent")}
 
 
 def parse():

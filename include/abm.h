@@ -239,11 +239,11 @@ abm_status  abm_dump_noalloc(abm_sim* sim, abm_record* out, size_t cap, size_t* 
 /* ---------------- profiling ---------------- */
 /* Runs n steps without the CUDA graph, with a CUDA event on the stream
  * before and after each of the step's kernels, and writes the summed time of
- * each kernel in milliseconds to kernel_ms[0..4] (n_kernels >= 5; names from
+ * each kernel in milliseconds to kernel_ms[0..5] (n_kernels >= 6; names from
  * abm_kernel_name).  Synchronous.  The state advances exactly as abm_step. */
 abm_status  abm_profile_step(abm_sim* sim, uint32_t n, float* kernel_ms, uint32_t n_kernels);
 abm_status  abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, uint32_t n_kernels);
-/* Name of step kernel k (0..4), or NULL. */
+/* Name of step kernel k (0..5), or NULL. */
 const char* abm_kernel_name(uint32_t k);
 
 /* ---------------- building blocks (host or debug) ---------------- */

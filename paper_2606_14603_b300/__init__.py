@@ -385,7 +385,7 @@ class Batch:
             pass
 
 
-N_STEP_KERNELS = 5
+N_STEP_KERNELS = 6
 
 
 def kernel_name(k: int) -> str:

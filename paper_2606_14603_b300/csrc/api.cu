@@ -243,7 +243,7 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
         16 * E, 4 * E, 8 * E,                  // extras
         16 * (size_t)Bc, 4 * (size_t)Bc,       // births
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
-        8 * tiles,                             // scan descriptors
+        4 * tiles,                             // tile sums / prefixes
         sizeof(SimDev) * S, sizeof(ModelDev) * S,
         8 * (size_t)S * 512, 8 * (size_t)S,    // counts, digests
         2 * 65536,                             // Gaussian table
@@ -518,7 +518,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.bpar = (uint32_t*)at();
     B.cnt = (uint32_t*)at();
     B.start = (uint32_t*)at();
-    B.tiles = (uint64_t*)at();
+    B.tsum = (uint32_t*)at();
     B.sims = (SimDev*)at();
     B.models = (ModelDev*)at();
     B.counts = (uint64_t*)at();
@@ -1106,7 +1106,7 @@ abm_status abm_profile_step(abm_sim* s, uint32_t n, float* kernel_ms, uint32_t n
     return s ? abm_batch_profile_step(s->b, n, kernel_ms, n_kernels) : ABM_EINVAL;
 }
 const char* abm_kernel_name(uint32_t k) {
-    static const char* names[] = {"k_move", "k_scan", "k_scatter", "k_propose", "k_accept"};
+    static const char* names[] = {"k_move", "k_tiles", "k_scan", "k_scatter", "k_propose", "k_accept"};
     return k < (uint32_t)kStepKernels ? names[k] : nullptr;
 }
 abm_status abm_step_index(abm_sim* s, uint32_t* out) {

@@ -11,7 +11,7 @@
 //   xpm/xid/xkr  released partners appended by the move pass (C/2 + 1)
 //   bpm/bpar     births of the step (B)
 //   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
-//   tiles[]      decoupled look-back descriptors of the scan
+//   tsum[T+1]    per-tile cell sums, then exclusive tile prefixes
 //   sims[S], models[S], obs (counts/digests), ctl
 //
 // meta word: bits 0-5 species, 6-7 compartment, 8 carrier, 9 carrier is
@@ -110,7 +110,7 @@ struct Ctl {
     uint32_t n_births;       // births of this step
     uint32_t cur;            // current buffer
     uint32_t n_cells;        // cells in use
-    uint32_t scan_ticket;
+    uint32_t scan_ticket;    // blocks of k_tiles finished this step
     uint32_t epoch;          // global step counter (look-back tags)
     uint32_t err;
     uint32_t err_info;
@@ -137,7 +137,7 @@ struct Buffers {
     uint32_t* bpar;
     uint32_t* cnt;
     uint32_t* start;
-    uint64_t* tiles;
+    uint32_t* tsum;
     SimDev* sims;
     ModelDev* models;
     uint64_t* counts;
@@ -248,8 +248,8 @@ cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s);
 cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim,
                         uint32_t base, uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp);
 cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest);
-// The step with a CUDA event before and after each of its kernels (ev[0..5]).
-constexpr int kStepKernels = 5;
+// The step with a CUDA event before and after each of its kernels (ev[0..6]).
+constexpr int kStepKernels = 6;
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev);
 // Between steps: drop the agents of retired simulations (counter: ctl.n_sorted).
 cudaError_t launch_compact(const Buffers& B, const Launch& L, cudaStream_t s);

@@ -1,12 +1,13 @@
 // kernels.cu — the per-step CUDA kernels (sm_103a) of the molecule-agent engine.
 //
 // One step (paper Sec. 2: diffusion, proximity binding, product release,
-// expression, degradation, compartment migration) is five launches over the
+// expression, degradation, compartment migration) is six launches over the
 // whole batch of simulations, all reading their sizes from the device
 // control block so that a captured CUDA graph replays them unchanged:
 //
 //   k_move      P1 events + P2 Brownian move + cell key + histogram rank
-//   k_scan      exclusive scan of the cell histogram (decoupled look-back)
+//   k_tiles     per-tile sums of the cell histogram, then tile prefixes
+//   k_scan      exclusive scan of the cell histogram within each tile
 //   k_scatter   reorder every live agent by cell into the other buffer
 //   k_propose   neighbour query over the cells a contact radius can reach,
 //               nearest eligible partner, atomicMin on a packed key
@@ -28,17 +29,13 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kScanV = kScanTile / kThreads;  // 32 cells per thread
-constexpr uint32_t kSpinLimit = 1u << 22;
 
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
+// Programmatic dependent launch: a step kernel may be launched while its
+// predecessor finishes; it waits here until the predecessor's grid has
+// completed and its writes are visible, and each block signals, when its
+// work is done, that the successor may start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
@@ -227,6 +224,7 @@ constexpr int kMoveILP = ABM_MOVE_ILP;
 
 __global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
     Ctl* ctl = B.ctl;
+    pdl_wait();
     if (ld_volatile(&ctl->err)) return;
     const uint32_t cur = ctl->cur;
     const uint32_t n = ctl->n_in;
@@ -268,27 +266,91 @@ __global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
         for (int u = 0; u < kMoveILP; u++)
             if (i0 + u * stride < n) move_phase4(B, ctl, cur, i0 + u * stride, a[u], rank[u]);
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------
-// k_scan: start[c] = sum of cnt[0..c), cnt reset to zero, single pass.
-// Tiles are taken from a ticket counter in launch order, so a tile only
-// waits for tiles whose owners are already running.  Each tile publishes
-// its aggregate, then its inclusive prefix, tagged with the step epoch.
-__global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
+// Exclusive block scan of one value per thread; returns the thread's
+// exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) {
+        const uint32_t sw = s_warp[w];
+        if (w < warp) wpre += sw;
+        tot += sw;
+    }
+    __syncthreads();  // s_warp may be reused by the caller
+    *total = tot;
+    return wpre + incl - v;
+}
+
+// ------------------------------------------------------------------------
+// The cell scan in two passes with no waiting between blocks.
+// k_tiles: tsum[t] = number of agents in cell tile t (8192 cells); the last
+// block to finish turns tsum into exclusive tile prefixes, writes the total
+// and the sorted-agent count.
+__global__ void __launch_bounds__(kThreads) k_tiles(Buffers B) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    __shared__ bool s_last;
     Ctl* ctl = B.ctl;
+    pdl_wait();
     if (ld_volatile(&ctl->err)) return;
     const uint32_t n = ctl->n_cells;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    const uint64_t epoch = (uint64_t)(ctl->epoch & 0x3FFFFFFFu);
-    __shared__ uint32_t s_tile, s_prefix, s_first;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint4* src = reinterpret_cast<const uint4*>(B.cnt + tile * kScanTile + threadIdx.x * kScanV);
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanV / 4; k++) {
+            const uint4 u = src[k];
+            sum += u.x + u.y + u.z + u.w;
+        }
+        uint32_t total;
+        block_exclusive_scan(sum, s_warp, &total);
+        if (threadIdx.x == 0) B.tsum[tile] = total;
+    }
+    pdl_trigger();
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctl->scan_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    uint32_t run = 0;
+    for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
+        const uint32_t t = base + threadIdx.x;
+        const uint32_t v = t < ntiles ? ld_volatile(&B.tsum[t]) : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, s_warp, &total);
+        if (t < ntiles) B.tsum[t] = run + ex;
+        run += total;
+    }
+    if (threadIdx.x == 0) {
+        B.tsum[ntiles] = run;
+        ctl->n_sorted = run;
+    }
+}
+
+// k_scan: start[c] = tile prefix + prefix of the tile's own counts; the
+// counts are reset to zero for the next step.
+__global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     __shared__ uint32_t s_warp[kThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->scan_ticket, 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) return;
+    Ctl* ctl = B.ctl;
+    pdl_wait();
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t n = ctl->n_cells;
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t base = tile * kScanTile + threadIdx.x * kScanV;
         uint32_t v[kScanV];
         uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
@@ -304,74 +366,8 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
         uint32_t tsum = 0;
 #pragma unroll
         for (int k = 0; k < kScanV; k++) tsum += v[k];
-        // block exclusive scan of the thread sums
-        uint32_t incl = tsum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        uint32_t wpre = 0, total = 0;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; w++) {
-            const uint32_t sw = s_warp[w];
-            if (w < warp) wpre += sw;
-            total += sw;
-        }
-        const uint32_t texcl = wpre + incl - tsum;
-        // publish the aggregate, then look back over up to 256 predecessor
-        // tiles per round (thread j reads tile k - j); the nearest tile that
-        // holds an inclusive prefix ends the walk
-        uint64_t* desc = B.tiles + tile;
-        if (threadIdx.x == 0) st_release(desc, epoch << 34 | (tile == 0 ? 2ull : 1ull) << 32 | total);
-        uint32_t excl = 0;
-        int64_t k = (int64_t)tile - 1;
-        bool timed_out = false;
-        while (k >= 0) {
-            const int64_t idx = k - threadIdx.x;
-            uint32_t st = 2, val = 0;
-            if (idx >= 0) {
-                uint32_t spins = 0;
-                for (;;) {
-                    const uint64_t d = ld_acquire(B.tiles + idx);
-                    st = (uint32_t)(d >> 32) & 3u;
-                    val = (uint32_t)d;
-                    if ((d >> 34) == epoch && st != 0) break;
-                    if (++spins > kSpinLimit) {
-                        timed_out = true;
-                        st = 2;
-                        val = 0;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            if (threadIdx.x == 0) s_first = kThreads;
-            __syncthreads();
-            if (st == 2) atomicMin(&s_first, (uint32_t)threadIdx.x);
-            __syncthreads();
-            const uint32_t first = s_first;
-            uint32_t part = threadIdx.x <= first ? val : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-            if (lane == 0) s_warp[warp] = part;
-            __syncthreads();
-#pragma unroll
-            for (int w = 0; w < kThreads / 32; w++) excl += s_warp[w];
-            __syncthreads();
-            if (first < (uint32_t)kThreads) break;
-            k -= kThreads;
-        }
-        if (timed_out) raise_error(ctl, ERR_TIMEOUT_SCAN, tile);
-        if (threadIdx.x == 0) {
-            if (tile != 0) st_release(desc, epoch << 34 | 2ull << 32 | (excl + total));
-            s_prefix = excl;
-        }
-        __syncthreads();
-        const uint32_t pre = s_prefix + texcl;
-        uint32_t run = pre;
+        uint32_t total;
+        uint32_t run = B.tsum[tile] + block_exclusive_scan(tsum, s_warp, &total);
         uint4* dst = reinterpret_cast<uint4*>(B.start + base);
 #pragma unroll
         for (int k = 0; k < kScanV / 4; k++) {
@@ -382,12 +378,9 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
             o.w = run; run += v[4 * k + 3];
             dst[k] = o;
         }
-        if (tile == ntiles - 1 && threadIdx.x == 0) {
-            B.start[n] = s_prefix + total;  // cells past n are empty
-            ctl->n_sorted = s_prefix + total;
-        }
-        __syncthreads();
+        if (tile == ntiles - 1 && threadIdx.x == 0) B.start[n] = B.tsum[ntiles];  // cells past n are empty
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------
@@ -398,6 +391,7 @@ constexpr int kScatterILP = 4;
 
 __global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
     Ctl* ctl = B.ctl;
+    pdl_wait();
     if (ld_volatile(&ctl->err)) return;
     const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
     const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
@@ -442,6 +436,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
             if (meta & M_BOUND) B.apar[nxt][dest[u]] = par[u];
         }
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------
@@ -499,6 +494,7 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     __shared__ uint32_t s_list[kProposeChunk];
     __shared__ uint32_t s_n;
     Ctl* ctl = B.ctl;
+    pdl_wait();
     if (ld_volatile(&ctl->err)) return;
     const uint32_t nxt = ctl->cur ^ 1u;
     const uint32_t n = ctl->n_sorted;
@@ -549,6 +545,7 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
         }
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------
@@ -634,6 +631,7 @@ __device__ void finalize_block(Buffers& B) {
 __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
     __shared__ bool s_last;
     Ctl* ctl = B.ctl;
+    pdl_wait();
     if (ld_volatile(&ctl->err)) return;
     const uint32_t nxt = ctl->cur ^ 1u;
     const uint32_t np = ctl->n_props;
@@ -668,6 +666,7 @@ __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
         *wa = ma;
         *wb = mb;
     }
+    pdl_trigger();
     // last-block-done: every block's writes are visible to the last one
     __threadfence();
     __syncthreads();
@@ -853,27 +852,48 @@ __global__ void k_debug_philox(const uint4* ctr, const uint2* key, uint4* out, s
 }  // namespace
 
 // ------------------------------------------------------------------------
+// Launch with programmatic stream serialisation: the kernel may begin
+// launching while the previous kernel in the stream drains (it waits in
+// pdl_wait before touching any data).
+template <typename Kernel>
+cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, B);
+}
+
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s) {
-    k_move<<<L.blocks_agents, kThreads, 0, s>>>(B);
-    k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
-    k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
-    k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
-    k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_move, L.blocks_agents, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_tiles, L.blocks_scan, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_scatter, L.blocks_agents, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_agents, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_accept, L.blocks_accept, s, B);
+    return e;
 }
 
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev) {
     cudaEventRecord(ev[0], s);
     k_move<<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[1], s);
-    k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
+    k_tiles<<<L.blocks_scan, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[2], s);
-    k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[3], s);
-    k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[4], s);
-    k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
+    k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[5], s);
+    k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
+    cudaEventRecord(ev[6], s);
     return cudaGetLastError();
 }
 
