@@ -216,6 +216,63 @@ abm_status  abm_batch_live_agents(abm_batch* b, uint64_t* out);  /* syncs */
 const char* abm_batch_last_error(const abm_batch* b);
 void        abm_batch_destroy(abm_batch* b);  /* NULL-safe */
 
+/* ---------------- threshold monitor ---------------- */
+/* Sec. 2 (simulator description): the user designates molecular species
+ * to follow continuously and sets a concentration threshold for a time
+ * window; the simulator then classifies the cell from whether the level
+ * passes it (the paper's ppERK example: above the healthy level early means
+ * aberrant signalling, and a drug that brings it back below means a return to
+ * normal).  Here a monitor watches one simulation:
+ *
+ *   value(t) = sum_k weights[k] * counts[k](t)
+ *
+ * over the counts layout above (free agents by species and compartment,
+ * bound complexes by reaction), at the state after t completed steps, for
+ * every t in [step_begin, step_end) with (t - step_begin) % period == 0.  A
+ * state passes when value > threshold (above = 1) or value < threshold
+ * (above = 0).  Each due state is evaluated exactly once: by the step that
+ * starts from it (the sum is taken inside that step's move kernel, so a
+ * monitor costs one weight lookup per agent and no extra pass over memory),
+ * or, for the state no step has started from yet, by abm_*_monitor_read.
+ * Results are exact integers and do not depend on when reads happen. */
+typedef struct {
+    uint32_t step_begin;     /* first step of the window                      */
+    uint32_t step_end;       /* one past the last; 0xFFFFFFFF = open-ended    */
+    uint32_t period;         /* >= 1                                          */
+    int32_t  above;          /* 1: passes when value > threshold, 0: < ...    */
+    int64_t  threshold;
+} abm_monitor;
+
+typedef struct {
+    int64_t  value;          /* value at the last evaluation                  */
+    uint32_t last_step;      /* step of the last evaluation                   */
+    uint32_t first_pass;     /* first evaluated step that passed, 0xFFFFFFFF = none */
+    uint32_t n_evaluated;
+    uint32_t n_passed;
+    int32_t  state;          /* last evaluation: 1 passed, 0 not, -1 none yet */
+    uint32_t reserved;
+} abm_monitor_state;
+
+/* Install (or replace, resetting its state) the monitor of a simulation.
+ * weights: n_weights <= counts length - 1 entries (the next-id entry is not a
+ * count), the rest taken as 0, each in [-2^20, 2^20].  ABM_EINVAL for bad
+ * weights, period 0 or step_end <= step_begin; ABM_ESTATE for a free slot.
+ * Synchronises.  Removing a simulation clears its monitor. */
+abm_status  abm_batch_monitor_set(abm_batch* b, int32_t sim_id, const abm_monitor* m,
+                                  const int32_t* weights, size_t n_weights);
+abm_status  abm_batch_monitor_clear(abm_batch* b, int32_t sim_id);   /* synchronises */
+/* State of the monitor after evaluating the current state if it is due,
+ * and the last min(n_evaluated, 1024) evaluated values, oldest first, in
+ * trace[0..cap) (*n_out = how many there are).  ABM_ESTATE without a
+ * monitor.  Synchronises. */
+abm_status  abm_batch_monitor_read(abm_batch* b, int32_t sim_id, abm_monitor_state* out,
+                                   int64_t* trace, size_t cap, size_t* n_out);
+abm_status  abm_monitor_set(abm_sim* sim, const abm_monitor* m, const int32_t* weights,
+                            size_t n_weights);
+abm_status  abm_monitor_clear(abm_sim* sim);
+abm_status  abm_monitor_read(abm_sim* sim, abm_monitor_state* out, int64_t* trace, size_t cap,
+                             size_t* n_out);
+
 /* ---------------- dump without allocation ---------------- */
 /* The same id-sorted records as abm_dump, for callers that cannot allocate
  * device memory at the time of the call: abm_dump allocates a device staging

@@ -8,6 +8,7 @@ library cannot be loaded or no sm_103 device is present, calls raise.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import os
 from typing import Optional
 
@@ -68,6 +69,32 @@ class BatchOptions(C.Structure):
                 ("blocks_per_sm", C.c_uint32)]
 
 
+class Monitor(C.Structure):
+    _fields_ = [("step_begin", C.c_uint32), ("step_end", C.c_uint32), ("period", C.c_uint32),
+                ("above", C.c_int32), ("threshold", C.c_int64)]
+
+
+class MonitorStateC(C.Structure):
+    _fields_ = [("value", C.c_int64), ("last_step", C.c_uint32), ("first_pass", C.c_uint32),
+                ("n_evaluated", C.c_uint32), ("n_passed", C.c_uint32), ("state", C.c_int32),
+                ("reserved", C.c_uint32)]
+
+
+@dataclasses.dataclass
+class MonitorState:
+    """A threshold monitor's state: the last evaluated value and step, the
+    first step that passed (None if none), counts, the last outcome (True /
+    False / None before any evaluation) and the evaluated values, oldest
+    first (the last 1024 at most)."""
+    value: int
+    last_step: int
+    first_pass: Optional[int]
+    n_evaluated: int
+    n_passed: int
+    state: Optional[bool]
+    trace: np.ndarray
+
+
 _lib = None
 
 
@@ -115,6 +142,13 @@ def lib():
             "abm_kernel_name": (C.c_char_p, [C.c_uint32]),
             "abm_grid_cells": (C.c_int, [P, C.POINTER(C.c_uint64)]),
             "abm_model_grid": (C.c_int, [C.POINTER(Model), C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
+            "abm_monitor_set": (C.c_int, [P, C.POINTER(Monitor), P, C.c_size_t]),
+            "abm_monitor_clear": (C.c_int, [P]),
+            "abm_monitor_read": (C.c_int, [P, C.POINTER(MonitorStateC), P, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "abm_batch_monitor_set": (C.c_int, [P, C.c_int32, C.POINTER(Monitor), P, C.c_size_t]),
+            "abm_batch_monitor_clear": (C.c_int, [P, C.c_int32]),
+            "abm_batch_monitor_read": (C.c_int, [P, C.c_int32, C.POINTER(MonitorStateC), P, C.c_size_t,
+                                                 C.POINTER(C.c_size_t)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -178,6 +212,37 @@ def model_grid(model, cell_log2: int = 0):
     sh, cells = C.c_uint32(), C.c_uint64()
     _check(lib().abm_model_grid(C.byref(ms.model), cell_log2, C.byref(sh), C.byref(cells)))
     return sh.value, cells.value
+
+
+def monitor_weights(model, species, include_bound: bool = True, compartments=None) -> np.ndarray:
+    """Weights over the counts vector that add up the given species (names or
+    indices): their free agents in the given compartments (all by default)
+    and, with include_bound, one per bound complex that contains one of them."""
+    names = [s.name for s in model.species]
+    idx = {names.index(s) if isinstance(s, str) else int(s) for s in species}
+    n_comp = len(model.compartments)
+    comps = range(n_comp) if compartments is None else compartments
+    w = np.zeros(len(model.species) * n_comp + len(model.reactions), dtype=np.int32)
+    for sp in idx:
+        for c in comps:
+            w[sp * n_comp + c] = 1
+    if include_bound:
+        for r, rx in enumerate(model.reactions):
+            w[len(model.species) * n_comp + r] = int(rx.a in idx) + int(rx.b in idx)
+    return w
+
+
+def _monitor_args(weights, threshold, above, begin, end, period):
+    w = np.ascontiguousarray(weights, dtype=np.int32)
+    m = Monitor(begin, 0xFFFFFFFF if end is None else end, period, 1 if above else 0, int(threshold))
+    return m, w
+
+
+def _monitor_state(st: MonitorStateC, trace: np.ndarray, n: int) -> MonitorState:
+    return MonitorState(int(st.value), int(st.last_step),
+                        None if st.first_pass == 0xFFFFFFFF else int(st.first_pass),
+                        int(st.n_evaluated), int(st.n_passed), None if st.state < 0 else bool(st.state),
+                        trace[:n].copy())
 
 
 def batch_capacity(models, headroom: float = 1.25, cell_log2_delta: int = 0):
@@ -258,6 +323,23 @@ class Sim:
         ms = np.zeros(8, dtype=np.float32)
         _check(lib().abm_profile_step(self._h, n, ms.ctypes.data, 8), lib().abm_last_error, self._h)
         return {kernel_name(k): float(ms[k]) for k in range(N_STEP_KERNELS)}
+
+    def monitor(self, weights, threshold: int, above: bool = True, begin: int = 0,
+                end: Optional[int] = None, period: int = 1) -> None:
+        """Install a threshold monitor: sum(weights * counts) against threshold
+        at steps begin, begin + period, ... below end (None = open)."""
+        m, w = _monitor_args(weights, threshold, above, begin, end, period)
+        _check(lib().abm_monitor_set(self._h, C.byref(m), w.ctypes.data if w.size else None, w.size),
+               lib().abm_last_error, self._h)
+
+    def monitor_clear(self) -> None:
+        _check(lib().abm_monitor_clear(self._h), lib().abm_last_error, self._h)
+
+    def monitor_read(self) -> MonitorState:
+        st, tr, n = MonitorStateC(), np.zeros(1024, dtype=np.int64), C.c_size_t()
+        _check(lib().abm_monitor_read(self._h, C.byref(st), tr.ctypes.data, tr.size, C.byref(n)),
+               lib().abm_last_error, self._h)
+        return _monitor_state(st, tr, n.value)
 
     def grid_cells(self) -> int:
         """Cells of this simulation's grid."""
@@ -361,6 +443,21 @@ class Batch:
         _check(lib().abm_batch_dump(self._h, sim, out.ctypes.data, out.size, C.byref(m)),
                lib().abm_batch_last_error, self._h)
         return out[: m.value]
+
+    def monitor(self, sim: int, weights, threshold: int, above: bool = True, begin: int = 0,
+                end: Optional[int] = None, period: int = 1) -> None:
+        m, w = _monitor_args(weights, threshold, above, begin, end, period)
+        _check(lib().abm_batch_monitor_set(self._h, sim, C.byref(m), w.ctypes.data if w.size else None, w.size),
+               lib().abm_batch_last_error, self._h)
+
+    def monitor_clear(self, sim: int) -> None:
+        _check(lib().abm_batch_monitor_clear(self._h, sim), lib().abm_batch_last_error, self._h)
+
+    def monitor_read(self, sim: int) -> MonitorState:
+        st, tr, n = MonitorStateC(), np.zeros(1024, dtype=np.int64), C.c_size_t()
+        _check(lib().abm_batch_monitor_read(self._h, sim, C.byref(st), tr.ctypes.data, tr.size, C.byref(n)),
+               lib().abm_batch_last_error, self._h)
+        return _monitor_state(st, tr, n.value)
 
     def profile_step(self, n: int = 1) -> dict:
         ms = np.zeros(8, dtype=np.float32)

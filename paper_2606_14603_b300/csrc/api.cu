@@ -246,6 +246,8 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
         4 * tiles,                             // tile sums / prefixes
         sizeof(SimDev) * S, sizeof(ModelDev) * S,
         8 * (size_t)S * 512, 8 * (size_t)S,    // counts, digests
+        sizeof(MonDev) * S, 4 * (size_t)S * 512,   // threshold monitors, their weights
+        8 * (size_t)S, 8 * (size_t)S * kMonTrace,  // monitor sums, evaluated values
         2 * 65536,                             // Gaussian table
         sizeof(Ctl),
         4 * kMaxSpecies,                       // staging for admissions
@@ -283,6 +285,7 @@ struct abm_batch {
         uint64_t n_cells = 0;
         uint32_t n_counts = 0;
         uint32_t shift = 0;
+        bool monitor = false;
     };
     std::vector<HostSim> sims;
     std::vector<uint32_t> cell_off_host;  // persistent sources of async copies
@@ -291,6 +294,9 @@ struct abm_batch {
     std::vector<ModelDev> model_host;   // copies of the uploaded model tables
     std::vector<int> model_refs;
     uint32_t n_sims_used = 0;
+    uint32_t n_monitors = 0;             // host copy of ctl.n_monitors (source of its upload)
+    MonDev mon_host{};                   // source of a monitor upload
+    std::vector<int32_t> mon_w_host;     // source of a weights upload
     bool failed = false;
     std::string err;
 };
@@ -523,6 +529,10 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.models = (ModelDev*)at();
     B.counts = (uint64_t*)at();
     B.digests = (uint64_t*)at();
+    B.mons = (MonDev*)at();
+    B.mon_w = (int32_t*)at();
+    B.mon_acc = (uint64_t*)at();
+    B.mon_trace = (int64_t*)at();
     int16_t* ztab = (int16_t*)at();
     B.ztab = ztab;
     B.ctl = (Ctl*)at();
@@ -811,11 +821,105 @@ abm_status abm_batch_remove(abm_batch* b, int32_t sim) {
     if (!b) return ABM_EINVAL;
     if (b->failed) return ABM_ESTATE;
     if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    if (b->sims[sim].monitor) {
+        abm_status st = abm_batch_monitor_clear(b, sim);
+        if (st != ABM_OK) return st;
+    }
     const uint32_t zero = 0;
     CU(cudaMemcpyAsync(&b->B.sims[sim].active, &zero, 4, cudaMemcpyHostToDevice, b->stream));
     b->sims[sim].state = 2;
     b->model_refs[b->sims[sim].model_slot]--;
     return repack_cells(b);
+}
+
+// ------------------------------------------------------------------------
+// Threshold monitors (one per simulation slot).
+abm_status abm_batch_monitor_set(abm_batch* b, int32_t sim, const abm_monitor* m, const int32_t* weights,
+                                 size_t n_weights) {
+    if (!b || !m || (n_weights && !weights)) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    // the last counts entry (next id) is not a count of records
+    if (n_weights > b->sims[sim].n_counts - 1 || m->period == 0 || m->step_end <= m->step_begin) {
+        b->err = "monitor: weights longer than the counts vector, period 0 or an empty window";
+        return ABM_EINVAL;
+    }
+    for (size_t k = 0; k < n_weights; k++)
+        if (weights[k] > (1 << 20) || weights[k] < -(1 << 20)) {
+            b->err = "monitor: weights must lie in [-2^20, 2^20]";
+            return ABM_EINVAL;
+        }
+    abm_status st = sync_and_check(b);
+    if (st != ABM_OK) return st;
+    b->mon_w_host.assign(512, 0);
+    std::copy(weights, weights + n_weights, b->mon_w_host.begin());
+    MonDev& M = b->mon_host;
+    M = MonDev{};
+    M.active = 1;
+    M.begin = m->step_begin;
+    M.end = m->step_end;
+    M.period = m->period;
+    M.threshold = m->threshold;
+    M.above = m->above ? 1u : 0u;
+    M.last_step = 0;
+    M.first_pass = kNone;
+    M.state = -1;
+    if (!b->sims[sim].monitor) b->n_monitors++;
+    b->sims[sim].monitor = true;
+    const uint64_t zero = 0;
+    CU(cudaMemcpyAsync(b->B.mon_w + (size_t)sim * 512, b->mon_w_host.data(), 4 * 512, cudaMemcpyHostToDevice,
+                       b->stream));
+    CU(cudaMemcpyAsync(b->B.mons + sim, &M, sizeof(MonDev), cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemcpyAsync(b->B.mon_acc + sim, &zero, 8, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemcpyAsync(&b->B.ctl->n_monitors, &b->n_monitors, 4, cudaMemcpyHostToDevice, b->stream));
+    return sync_and_check(b);
+}
+
+abm_status abm_batch_monitor_clear(abm_batch* b, int32_t sim) {
+    if (!b) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    if (!b->sims[sim].monitor) return ABM_OK;
+    abm_status st = sync_and_check(b);
+    if (st != ABM_OK) return st;
+    b->sims[sim].monitor = false;
+    b->n_monitors--;
+    const uint32_t zero = 0;
+    CU(cudaMemcpyAsync(&b->B.mons[sim].active, &zero, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemcpyAsync(&b->B.ctl->n_monitors, &b->n_monitors, 4, cudaMemcpyHostToDevice, b->stream));
+    return sync_and_check(b);
+}
+
+abm_status abm_batch_monitor_read(abm_batch* b, int32_t sim, abm_monitor_state* out, int64_t* trace, size_t cap,
+                                  size_t* n_out) {
+    if (!b || !out || (cap && !trace)) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    if (!b->sims[sim].monitor) {
+        b->err = "monitor: no threshold monitor on this simulation";
+        return ABM_ESTATE;
+    }
+    CU(launch_monitor(b->B, b->L, b->stream, sim));
+    MonDev M;
+    std::vector<int64_t> ring(kMonTrace);
+    CU(cudaMemcpyAsync(&M, b->B.mons + sim, sizeof(MonDev), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaMemcpyAsync(ring.data(), b->B.mon_trace + (size_t)sim * kMonTrace, 8 * kMonTrace,
+                       cudaMemcpyDeviceToHost, b->stream));
+    abm_status st = sync_and_check(b);
+    if (st != ABM_OK) return st;
+    out->value = M.value;
+    out->last_step = M.last_step;
+    out->first_pass = M.first_pass;
+    out->n_evaluated = M.n_eval;
+    out->n_passed = M.n_passed;
+    out->state = M.state;
+    out->reserved = 0;
+    // oldest first: the ring holds the last min(n_eval, kMonTrace) values
+    const uint32_t kept = std::min<uint32_t>(M.n_eval, kMonTrace);
+    if (n_out) *n_out = kept;
+    const size_t want = std::min<size_t>(cap, kept);
+    for (size_t k = 0; k < want; k++) trace[k] = ring[(M.n_eval - kept + k) % kMonTrace];
+    return ABM_OK;
 }
 
 abm_status abm_batch_set_max_step(abm_batch* b, int32_t sim, uint32_t max_step) {
@@ -1102,6 +1206,13 @@ abm_status abm_dump(abm_sim* s, abm_record* out, size_t cap, size_t* n_out) {
     return s ? abm_batch_dump(s->b, s->id, out, cap, n_out) : ABM_EINVAL;
 }
 abm_status abm_sync(abm_sim* s) { return s ? abm_batch_sync(s->b) : ABM_EINVAL; }
+abm_status abm_monitor_set(abm_sim* s, const abm_monitor* m, const int32_t* weights, size_t n_weights) {
+    return s ? abm_batch_monitor_set(s->b, s->id, m, weights, n_weights) : ABM_EINVAL;
+}
+abm_status abm_monitor_clear(abm_sim* s) { return s ? abm_batch_monitor_clear(s->b, s->id) : ABM_EINVAL; }
+abm_status abm_monitor_read(abm_sim* s, abm_monitor_state* out, int64_t* trace, size_t cap, size_t* n_out) {
+    return s ? abm_batch_monitor_read(s->b, s->id, out, trace, cap, n_out) : ABM_EINVAL;
+}
 abm_status abm_profile_step(abm_sim* s, uint32_t n, float* kernel_ms, uint32_t n_kernels) {
     return s ? abm_batch_profile_step(s->b, n, kernel_ms, n_kernels) : ABM_EINVAL;
 }

@@ -31,6 +31,7 @@ constexpr int kMaxSims = 2048;
 constexpr uint32_t kMaxBirths = 8192;
 constexpr int kScanTile = 8192;           // cells per scan tile (256 threads x 32)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kMonTrace = 1024;      // evaluations kept per threshold monitor
 constexpr uint64_t kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint64_t kInvalidKey = 0xFFFFFFFFFFFFFFFFull;
 
@@ -103,6 +104,21 @@ struct SimDev {              // per simulation slot
     uint32_t pad[2];
 };
 
+// Threshold monitor of one simulation slot (Sec. 2: designated species
+// followed against a threshold inside a time window).  value(t) = sum over
+// the counts vector of weight * count at the state after t completed steps.
+struct MonDev {
+    uint32_t active;
+    uint32_t begin, end, period;   // evaluated at t in [begin, end), (t - begin) % period == 0
+    int64_t threshold;
+    uint32_t above;          // 1: passes when value > threshold; 0: when value < threshold
+    uint32_t n_eval, n_passed;
+    uint32_t last_step;      // step of the last evaluation
+    uint32_t first_pass;     // first evaluated step that passed, kNone = none
+    int32_t state;           // outcome of the last evaluation, -1 = none yet
+    int64_t value;           // value at the last evaluation
+};
+
 struct Ctl {
     uint32_t n_in;           // agents in the current buffer
     uint32_t n_extra;        // released partners of this step
@@ -116,7 +132,7 @@ struct Ctl {
     uint32_t err_info;
     uint32_t n_sims;         // sim slots in use (upper bound of the table)
     uint32_t dump_n;
-    uint32_t pad0;
+    uint32_t n_monitors;     // simulations with an active threshold monitor
     uint32_t blocks_done;    // blocks of k_accept finished this step
     uint32_t n_props;        // proposals of this step (list in props)
     uint32_t pad;
@@ -142,6 +158,10 @@ struct Buffers {
     ModelDev* models;
     uint64_t* counts;
     uint64_t* digests;
+    MonDev* mons;            // [max_sims]
+    int32_t* mon_w;          // [max_sims][512] weights over the counts vector
+    uint64_t* mon_acc;       // [max_sims] running sums (two's complement)
+    int64_t* mon_trace;      // [max_sims][kMonTrace] ring of evaluated values
     const int16_t* ztab;
     Ctl* ctl;
     uint64_t cap_agents;
@@ -234,6 +254,20 @@ __device__ __forceinline__ void raise_error(Ctl* ctl, uint32_t code, uint32_t in
     if (atomicCAS(&ctl->err, 0u, code) == 0u) ctl->err_info = info;
 }
 
+// Index of a live record in the counts vector: free agents by (species,
+// compartment), bound carriers by reaction (one entry per bound pair).
+__device__ __forceinline__ uint32_t count_slot(uint32_t meta, const ModelDev& Mo) {
+    if (meta & M_BOUND) return Mo.n_sp * Mo.n_comp + ((meta & M_RXN) >> M_RXN_SHIFT);
+    return (meta & M_SP) * Mo.n_comp + ((meta & M_COMP) >> M_COMP_SHIFT);
+}
+
+// Whether a monitor evaluates the state after t completed steps (each such
+// state at most once, whether in a step or at a read between steps).
+__device__ __forceinline__ bool mon_due(const MonDev& M, uint32_t t) {
+    return M.active && t >= M.begin && t < M.end && (t - M.begin) % M.period == 0 &&
+           (M.n_eval == 0 || t > M.last_step);
+}
+
 // ------------------------------------------------------------------------
 // Host-side launch wrappers (kernels.cu).
 struct Launch {
@@ -255,6 +289,9 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
 cudaError_t launch_compact(const Buffers& B, const Launch& L, cudaStream_t s);
 cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim, void* d_out,
                         uint32_t cap);
+// Threshold monitor of one simulation at the current state (between steps):
+// adds up its value if that state is due and not yet evaluated, then evaluates.
+cudaError_t launch_monitor(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim);
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                                 cudaStream_t s);
 

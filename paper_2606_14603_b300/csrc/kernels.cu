@@ -94,6 +94,63 @@ struct MoveState {
     uint32_t key;
 };
 
+// Warp-aggregated add of each lane's monitor weight to its simulation's sum:
+// the lanes of a warp nearly always belong to one simulation.
+__device__ __forceinline__ void monitor_add(uint64_t* acc, uint32_t s, int32_t w) {
+    const uint32_t mask = __activemask();
+    const bool has = s != kNone && w != 0;
+    const uint32_t live = __ballot_sync(mask, has);
+    if (!live) return;
+    const uint32_t s0 = __shfl_sync(mask, s, __ffs(live) - 1);
+    const bool grp = has && s == s0;
+    const uint32_t gmask = __ballot_sync(mask, grp);
+    if (grp) {
+        const int32_t sum = __reduce_add_sync(gmask, w);  // |w| <= 2^20: no overflow
+        if ((threadIdx.x & 31u) == (uint32_t)(__ffs(gmask) - 1))
+            atomicAdd((unsigned long long*)&acc[s0], (unsigned long long)(int64_t)sum);
+    } else if (has) {
+        atomicAdd((unsigned long long*)&acc[s], (unsigned long long)(int64_t)w);
+    }
+}
+
+// A record's contribution to its simulation's monitor, if that monitor is
+// due at the simulation's current step (only: a simulation, or kNone = any).
+__device__ __forceinline__ void monitor_record(Buffers& B, uint32_t meta, uint32_t only) {
+    uint32_t s = kNone;
+    int32_t w = 0;
+    if (!(meta & (M_DEAD | M_ABSORBED))) {
+        const uint32_t sm = sim_of(meta);
+        const SimDev& S = B.sims[sm];
+        if ((only == kNone || sm == only) && S.active && mon_due(B.mons[sm], S.step)) {
+            s = sm;
+            w = B.mon_w[(size_t)sm * 512 + count_slot(meta, B.models[S.model])];
+        }
+    }
+    monitor_add(B.mon_acc, s, w);
+}
+
+// Evaluates simulation s's monitor if the current state is due; run by one
+// thread per simulation after every contribution has been added.
+__device__ __forceinline__ void monitor_eval(Buffers& B, uint32_t s) {
+    const SimDev& S = B.sims[s];
+    if (!S.active) return;
+    MonDev& M = B.mons[s];
+    const uint32_t t = S.step;
+    if (!mon_due(M, t)) return;
+    const int64_t v = (int64_t)B.mon_acc[s];
+    B.mon_acc[s] = 0;
+    const bool passed = M.above ? v > M.threshold : v < M.threshold;
+    B.mon_trace[(size_t)s * kMonTrace + M.n_eval % kMonTrace] = v;
+    M.n_eval += 1;
+    M.last_step = t;
+    M.value = v;
+    M.state = passed ? 1 : 0;
+    if (passed) {
+        M.n_passed += 1;
+        if (M.first_pass == kNone) M.first_pass = t;
+    }
+}
+
 // Phase 1: P1 events (a released partner is moved and placed right away:
 // rare) and the move draw; issues the three table loads.
 __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, uint32_t par, MoveState& a) {
@@ -222,7 +279,7 @@ __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, 
 #endif
 constexpr int kMoveILP = ABM_MOVE_ILP;
 
-__global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
+__global__ void __launch_bounds__(kThreads, 5) k_move(Buffers B) {
     Ctl* ctl = B.ctl;
     pdl_wait();
     if (ld_volatile(&ctl->err)) return;
@@ -239,6 +296,12 @@ __global__ void __launch_bounds__(kThreads) k_move(Buffers B) {
     const uint32_t np = ctl->n_props;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
+    // threshold monitors add up the records as they stand after t steps (a
+    // loop of its own: it keeps the main loop's register count; the main loop
+    // then finds these records in L1)
+    if (ctl->n_monitors)
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            monitor_record(B, (uint32_t)pm[i].w, kNone);
     // kMoveILP agents per thread, phase by phase, so that their loads, table
     // lookups and histogram atomics overlap
     for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kMoveILP * stride) {
@@ -611,6 +674,8 @@ __device__ void finalize_block(Buffers& B) {
         if (k < nb && gt[q] == 0) B.sims[mine[q] >> 32].next_id += lt[q] + 1;  // one writer per sim
     }
     const uint32_t n_sims = ctl->n_sims;
+    if (ctl->n_monitors)  // k_move added up the state this step started from
+        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x) monitor_eval(B, s);
     for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
         if (B.sims[s].active && B.sims[s].step < B.sims[s].max_step) B.sims[s].step += 1;
     __syncthreads();
@@ -790,6 +855,21 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
     }
 }
 
+// k_monitor_pass / k_monitor_eval: between steps, the same sum for one
+// simulation's current state (a state no step has evaluated yet, e.g. the
+// last one), then its evaluation.
+__global__ void __launch_bounds__(kThreads) k_monitor_pass(Buffers B, uint32_t sim) {
+    Ctl* ctl = B.ctl;
+    const uint32_t cur = ctl->cur;
+    const uint32_t n = ctl->n_in;
+    const SimDev& S = B.sims[sim];
+    if (!S.active || !mon_due(B.mons[sim], S.step)) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        monitor_record(B, (uint32_t)B.pm[cur][i].w, sim);
+}
+
+__global__ void k_monitor_eval(Buffers B, uint32_t sim) { monitor_eval(B, sim); }
+
 // k_compact: between steps, copy the agents of active simulations (dropping
 // those of retired ones) to the other buffer; storage order is free.
 __global__ void __launch_bounds__(kThreads) k_compact(Buffers B) {
@@ -913,6 +993,12 @@ cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, in
 
 cudaError_t launch_compact(const Buffers& B, const Launch& L, cudaStream_t s) {
     k_compact<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_monitor(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim) {
+    k_monitor_pass<<<L.blocks_agents, kThreads, 0, s>>>(B, (uint32_t)sim);
+    k_monitor_eval<<<1, 1, 0, s>>>(B, (uint32_t)sim);
     return cudaGetLastError();
 }
 
