@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=20.0,
                    help="seconds of job arrivals in the serving measurement (the served config runs 600)")
     p.add_argument("--sweep-steps", type=int, default=50, help="steps per sim in the sweep summary")
+    p.add_argument("--volume-steps", type=int, default=4000,
+                   help="steps of the volume-invariance summary (1M vs 10M agents per dose; 0 = skip)")
     p.add_argument("--agents", type=int, default=0, help="override the agent count")
     p.add_argument("--profile-steps", type=int, default=50)
     p.add_argument("--no-flush", action="store_true", help="do not flush L2 between steps")
@@ -444,6 +446,16 @@ def main():
         served = run_serve(A, args.serve_seconds)
         sim = None
 
+    volume = None
+    if args.volume_steps > 0 and args.workload == "cascade" and not args.agents:
+        from paper_2606_14603_b300.experiments import volume_invariance
+        import workloads as W
+        volume = volume_invariance(lambda n, d: W.mapk(n, d), [0.0, 0.02, 0.05, 0.10], 1_000_000,
+                                   factor=10, steps=args.volume_steps, stream=stream)
+        volume["note"] = ("cascade at 1x (1M agents per dose) and 10x volume (10M) at the same "
+                          "concentrations, one batch per volume; change_pct = final vs initial "
+                          "pERK+ppERK (free + in complexes), percent")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(model, seed, name)
@@ -458,7 +470,7 @@ def main():
             "roofline": roof, "step_roofline": step_roof,
             "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
             "gpu_launches": A.N_STEP_KERNELS * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
-            "serve": served,
+            "serve": served, "volume": volume,
             "clocks": clocks, "wall_s_timed_region": wall}
     if rank == 0:
         print(json.dumps(line), flush=True)
