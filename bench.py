@@ -229,7 +229,7 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0):
     sims = W.sweep(scale)
     models = [m for m, _ in sims]
     n_total = sum(m.n_agents for m in models)
-    best, tried = autotune.tune(sims, cell_deltas=(0, 1), blocks=(8, 16, 32), steps=10, warmup=2)
+    best, tried = autotune.tune(sims, cell_deltas=(0, 1), blocks=(0, 16, 32), steps=10, warmup=2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     b, ids = autotune.batch_for(sims, best.cell_delta, best.blocks_per_sm, stream=stream)
     b.step(warmup)

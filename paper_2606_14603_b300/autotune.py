@@ -19,7 +19,7 @@ from . import Batch, model_grid
 @dataclasses.dataclass
 class Choice:
     cell_delta: int          # added to each model's automatic cell_log2
-    blocks_per_sm: int
+    blocks_per_sm: int       # 0 = the CTAs of the move pass that fit on an SM at once
     ms_per_step: float
 
 
@@ -44,7 +44,7 @@ def batch_for(sims: Sequence[Tuple[object, int]], cell_delta: int = 0, blocks_pe
     return b, ids
 
 
-def tune(sims: Sequence[Tuple[object, int]], cell_deltas=(-1, 0, 1), blocks=(8, 16, 32),
+def tune(sims: Sequence[Tuple[object, int]], cell_deltas=(-1, 0, 1), blocks=(0, 8, 16),
          steps: int = 20, warmup: int = 3) -> Tuple[Choice, List[Choice]]:
     import torch
     stream = torch.cuda.Stream()

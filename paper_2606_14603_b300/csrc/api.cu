@@ -551,8 +551,17 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t want = (b->cap_agents + 255) / 256;
     b->L.threads = 256;
-    const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : 16;
+    // the move and scatter passes run best with exactly the CTAs that fit at
+    // once (a grid-stride loop, no tail wave); the proposal search with one
+    // chunk of sorted agents per CTA, so that the hardware balances chunks of
+    // unequal work, and chunks large enough to amortise their compaction
+    const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm();
     b->L.blocks_agents = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * per_sm));
+    uint64_t chunk = 1024;
+    while (chunk < 4096 && chunk * (uint64_t)sms * 8 < b->cap_agents) chunk *= 2;
+    B.propose_chunk = (uint32_t)chunk;
+    b->L.blocks_propose =
+        (int)std::max<uint64_t>(1, std::min<uint64_t>((b->cap_agents + chunk - 1) / chunk, (uint64_t)sms * 32));
     b->L.blocks_scan = (int)std::max<uint64_t>(1, std::min<uint64_t>(B.n_tiles_max, (uint64_t)sms * 4));
     b->L.blocks_accept = sms;
 
@@ -703,38 +712,33 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
         }
         c->n0 = rs.pm.size();  // agents to place
     }
-    // slot: a free one (draining slots become free after the next step)
-    int32_t slot = -1;
-    for (uint32_t s = 0; s < b->max_sims; s++)
-        if (b->sims[s].state == 0) {
-            slot = (int32_t)s;
-            break;
-        }
-    if (slot < 0 || cells_in_use(b) + ncell > b->cap_cells) {
-        b->err = slot < 0 ? "no free simulation slot" : "grid cells exhausted";
-        delete c;
-        return ABM_ECAPACITY;
-    }
     Ctl h;
     st = sync_and_check(b, &h);
     if (st != ABM_OK) {
         delete c;
         return st;
     }
-    if ((uint64_t)h.n_in + c->n0 > b->cap_agents) {
-        // agents of retired sims still occupy slots until the next step: drop them now
-        bool draining = false;
-        for (uint32_t s = 0; s < b->max_sims; s++) draining |= b->sims[s].state == 2;
-        if (draining) {
-            st = compact(b, &h);
-            if (st != ABM_OK) {
-                delete c;
-                return st;
-            }
+    auto free_slot = [&]() -> int32_t {
+        for (uint32_t s = 0; s < b->max_sims; s++)
+            if (b->sims[s].state == 0) return (int32_t)s;
+        return -1;
+    };
+    // retired sims keep their slot and agents until the next step drops them;
+    // when either is needed now, drop them here
+    int32_t slot = free_slot();
+    bool draining = false;
+    for (uint32_t s = 0; s < b->max_sims; s++) draining |= b->sims[s].state == 2;
+    if (draining && (slot < 0 || (uint64_t)h.n_in + c->n0 > b->cap_agents)) {
+        st = compact(b, &h);
+        if (st != ABM_OK) {
+            delete c;
+            return st;
         }
+        slot = free_slot();
     }
-    if ((uint64_t)h.n_in + c->n0 > b->cap_agents) {
-        b->err = "agent capacity exhausted";
+    if (slot < 0 || cells_in_use(b) + ncell > b->cap_cells || (uint64_t)h.n_in + c->n0 > b->cap_agents) {
+        b->err = slot < 0 ? "no free simulation slot"
+                 : cells_in_use(b) + ncell > b->cap_cells ? "grid cells exhausted" : "agent capacity exhausted";
         delete c;
         return ABM_ECAPACITY;
     }

@@ -169,6 +169,7 @@ struct Buffers {
     uint64_t cap_cells;
     uint32_t cap_births;
     uint32_t n_tiles_max;
+    uint32_t propose_chunk;  // sorted agents per proposal-search block round (multiple of 256)
 };
 
 // ------------------------------------------------------------------------
@@ -275,7 +276,11 @@ struct Launch {
     int threads;             // 256
     int blocks_scan;
     int blocks_accept;       // CTAs of the acceptance kernel (walks the proposal list)
+    int blocks_propose;      // CTAs of the proposal search, one chunk of sorted agents each
 };
+
+// CTAs of k_move that fit on one SM at once (its registers decide).
+int move_blocks_per_sm();
 
 cudaError_t prepare_kernels();
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s);

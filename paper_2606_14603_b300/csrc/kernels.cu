@@ -551,10 +551,8 @@ __device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida
 // range of the cell-sorted array -- keeps the nearest eligible partner by
 // (dist^2, id) and claims it with atomicMin.  Any partner within a contact
 // radius lies inside that box, so the result equals the 27-cell search.
-constexpr int kProposeChunk = 4 * kThreads;  // sorted agents examined per block round
-
 __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
-    __shared__ uint32_t s_list[kProposeChunk];
+    extern __shared__ uint32_t s_list[];  // B.propose_chunk entries
     __shared__ uint32_t s_n;
     Ctl* ctl = B.ctl;
     pdl_wait();
@@ -565,12 +563,12 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     const uint32_t* __restrict__ aid = B.aid[nxt];
     const uint32_t* __restrict__ start = B.start;
     const int lane = threadIdx.x & 31;
-    for (uint32_t base = blockIdx.x * kProposeChunk; base < n; base += gridDim.x * kProposeChunk) {
+    const uint32_t chunk = B.propose_chunk;
+    for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk) {
         if (threadIdx.x == 0) s_n = 0;
         __syncthreads();
         // compact the chunk's free agents of proposing species into s_list
-#pragma unroll
-        for (int u = 0; u < kProposeChunk / kThreads; u++) {
+        for (uint32_t u = 0; u < chunk / kThreads; u++) {
             const uint32_t i = base + u * kThreads + threadIdx.x;
             const bool isp = i < n && B.pflag[i];
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isp);
@@ -936,11 +934,11 @@ __global__ void k_debug_philox(const uint4* ctr, const uint2* key, uint4* out, s
 // launching while the previous kernel in the stream drains (it waits in
 // pdl_wait before touching any data).
 template <typename Kernel>
-cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B) {
+cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B, size_t smem = 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -950,12 +948,18 @@ cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B
     return cudaLaunchKernelEx(&cfg, kernel, B);
 }
 
+int move_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move, kThreads, 0) != cudaSuccess || n < 1) n = 4;
+    return n;
+}
+
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s) {
     cudaError_t e = launch_pdl(k_move, L.blocks_agents, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_tiles, L.blocks_scan, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_scatter, L.blocks_agents, s, B);
-    if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_agents, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, 4 * (size_t)B.propose_chunk);
     if (e == cudaSuccess) e = launch_pdl(k_accept, L.blocks_accept, s, B);
     return e;
 }
@@ -970,7 +974,7 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
     cudaEventRecord(ev[3], s);
     k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[4], s);
-    k_propose<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    k_propose<<<L.blocks_propose, kThreads, 4 * (size_t)B.propose_chunk, s>>>(B);
     cudaEventRecord(ev[5], s);
     k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[6], s);

@@ -263,6 +263,33 @@ def test_admission_right_after_removal_compacts(A, oracle_mod):
     b.close()
 
 
+def test_admission_reuses_a_retired_slot_before_any_step(A, oracle_mod):
+    """Every slot taken; retiring one frees it for an admission right away
+    (the admission drops the retired agents itself), several times between
+    two steps, as a server retiring and admitting jobs does."""
+    toys = [W.toy(300 + 10 * k, 300, edge_um=0.4) for k in range(5)]
+    cells = 2 * max(A.model_grid(m)[1] for m in toys)
+    b = A.Batch(4_000, cells, 2)
+    s0 = b.add(toys[0], 10)
+    s1 = b.add(toys[1], 11)
+    b.step(5)
+    b.remove(s0)
+    s2 = b.add(toys[2], 12)                # no step since the removal
+    b.remove(s2)
+    s3 = b.add(toys[3], 13)
+    b.step(7)
+    o1 = oracle_mod.OracleSim(toys[1], 11)
+    o1.step(12)
+    o3 = oracle_mod.OracleSim(toys[3], 13)
+    o3.step(7)
+    assert b.digest(s1) == o1.digest()
+    assert b.digest(s3) == o3.digest()
+    with pytest.raises(A.AbmError) as e:
+        b.add(toys[4], 14)                 # both slots live: no slot
+    assert e.value.status == A.ECAPACITY
+    b.close()
+
+
 @pytest.mark.parametrize("which", ["mapk", "nuclear"])
 def test_checkpoint_restore_continues_bit_exact(A, oracle_mod, which):
     if which == "mapk":
