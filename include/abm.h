@@ -129,8 +129,9 @@ typedef struct {
     size_t         arena_bytes;
     void*          stream;
     const int16_t* ncdf_table;
-    uint32_t       blocks_per_sm;    /* CTAs of 256 threads per SM for the per-agent
-                                        kernels (grid-stride); 0 = 16 */
+    uint32_t       blocks_per_sm;    /* CTAs of 256 threads per SM for the move and
+                                        scatter kernels (grid-stride); 0 = as many
+                                        as fit on an SM at once */
 } abm_batch_options;
 
 /* Layout of abm_*_counts output (uint64 each):

@@ -362,7 +362,6 @@ abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
         case ERR_CAPACITY_AGENTS: what = "agent capacity exceeded"; break;
         case ERR_CAPACITY_EXTRAS: what = "release buffer capacity exceeded"; break;
         case ERR_CAPACITY_BIRTHS: what = "births per step exceed the limit"; break;
-        case ERR_TIMEOUT_SCAN: what = "scan look-back wait timed out"; st = ABM_ETIMEOUT; break;
         case ERR_PLACEMENT: what = "could not place an agent in its compartment"; st = ABM_EINVAL; break;
         case ERR_ID_SPACE: what = "agent id space exhausted"; break;
         default: what = "device error"; st = ABM_ECUDA; break;

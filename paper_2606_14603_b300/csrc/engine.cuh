@@ -51,7 +51,6 @@ enum : uint32_t {
     ERR_CAPACITY_AGENTS = 1,
     ERR_CAPACITY_EXTRAS = 2,
     ERR_CAPACITY_BIRTHS = 3,
-    ERR_TIMEOUT_SCAN = 4,
     ERR_PLACEMENT = 5,
     ERR_ID_SPACE = 6,
     ERR_CAPACITY_DUMP = 7,
@@ -284,6 +283,7 @@ int move_blocks_per_sm();
 
 cudaError_t prepare_kernels();
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s);
+
 cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim,
                         uint32_t base, uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp);
 cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest);

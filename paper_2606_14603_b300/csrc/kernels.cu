@@ -81,8 +81,8 @@ __device__ __forceinline__ void brownian_move(const SimDev& S, const SpeciesDev&
 // k_move: P1 first-order events and P2 move for every agent of the current
 // buffer, then the cell key and the agent's rank inside its cell (the value
 // returned by the histogram atomic), which the scatter uses directly.
-// Work of one agent of the move pass, split into phases so that a thread can
-// keep the memory round trips of several agents in flight at once.
+// Work of one agent of the move pass, in phases: events and the move draw,
+// the step itself, then the results.
 struct MoveState {
     int4 p;              // record, moved in place
     uint32_t id;
@@ -251,7 +251,7 @@ __device__ __forceinline__ void move_phase2(MoveState& a) {
     a.key = cell_of(S, a.p.x, a.p.y, a.p.z);
 }
 
-// Phase 4: results (the histogram rank comes from phase 3) and births.
+// Phase 4: results (the histogram rank comes from the atomic between) and births.
 __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, const MoveState& a,
                                             uint32_t rank) {
     if (!(a.flags & 1u)) {
@@ -274,18 +274,12 @@ __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, 
     }
 }
 
-#ifndef ABM_MOVE_ILP
-#define ABM_MOVE_ILP 1
-#endif
-constexpr int kMoveILP = ABM_MOVE_ILP;
 
-__global__ void __launch_bounds__(kThreads, 5) k_move(Buffers B) {
+__device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
-    pdl_wait();
-    if (ld_volatile(&ctl->err)) return;
     const uint32_t cur = ctl->cur;
     const uint32_t n = ctl->n_in;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
         ctl->scan_ticket = 0;
         ctl->n_sorted = 0;  // the scan's last tile writes the real count
     }
@@ -294,41 +288,46 @@ __global__ void __launch_bounds__(kThreads, 5) k_move(Buffers B) {
     const uint32_t* __restrict__ apar = B.apar[cur];
     // proposal slots touched last step become empty again (the list is short)
     const uint32_t np = ctl->n_props;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
+    const uint32_t stride = nb * blockDim.x;
+    for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
     // threshold monitors add up the records as they stand after t steps (a
     // loop of its own: it keeps the main loop's register count; the main loop
     // then finds these records in L1)
     if (ctl->n_monitors)
-        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        for (uint32_t i = bid * blockDim.x + threadIdx.x; i < n; i += stride)
             monitor_record(B, (uint32_t)pm[i].w, kNone);
-    // kMoveILP agents per thread, phase by phase, so that their loads, table
-    // lookups and histogram atomics overlap
-    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kMoveILP * stride) {
-        MoveState a[kMoveILP];
-        uint32_t par[kMoveILP];
-#pragma unroll
-        for (int u = 0; u < kMoveILP; u++) {
-            const uint32_t i = i0 + u * stride;
-            a[u].flags = 0;
-            if (i < n) {
-                a[u].p = pm[i];
-                a[u].id = aid[i];
-                par[u] = apar[i];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kMoveILP; u++)
-            if (i0 + u * stride < n) move_phase1(B, ctl, i0 + u * stride, par[u], a[u]);
-#pragma unroll
-        for (int u = 0; u < kMoveILP; u++) move_phase2(a[u]);
-        uint32_t rank[kMoveILP];
-#pragma unroll
-        for (int u = 0; u < kMoveILP; u++) rank[u] = (a[u].flags & 1u) ? atomicAdd(&B.cnt[a[u].key], 1u) : 0u;
-#pragma unroll
-        for (int u = 0; u < kMoveILP; u++)
-            if (i0 + u * stride < n) move_phase4(B, ctl, cur, i0 + u * stride, a[u], rank[u]);
+    // one agent per iteration; the next agent's record is loaded while this
+    // one runs its chain of dependent table lookups and the histogram atomic
+    uint32_t i = bid * blockDim.x + threadIdx.x;
+    int4 nx_p = make_int4(0, 0, 0, 0);
+    uint32_t nx_id = 0, nx_par = 0;
+    if (i < n) {
+        nx_p = pm[i];
+        nx_id = aid[i];
+        nx_par = apar[i];
     }
+    for (; i < n; i += stride) {
+        MoveState a;
+        a.p = nx_p;
+        a.id = nx_id;
+        const uint32_t par = nx_par;
+        const uint32_t j = i + stride;
+        if (j < n) {
+            nx_p = pm[j];
+            nx_id = aid[j];
+            nx_par = apar[j];
+        }
+        move_phase1(B, ctl, i, par, a);
+        move_phase2(a);
+        const uint32_t rank = (a.flags & 1u) ? atomicAdd(&B.cnt[a.key], 1u) : 0u;
+        move_phase4(B, ctl, cur, i, a, rank);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_move(Buffers B) {
+    pdl_wait();
+    if (ld_volatile(&B.ctl->err)) return;
+    move_pass(B, blockIdx.x, gridDim.x);
     pdl_trigger();
 }
 
@@ -359,18 +358,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 
 // ------------------------------------------------------------------------
 // The cell scan in two passes with no waiting between blocks.
-// k_tiles: tsum[t] = number of agents in cell tile t (8192 cells); the last
-// block to finish turns tsum into exclusive tile prefixes, writes the total
-// and the sorted-agent count.
-__global__ void __launch_bounds__(kThreads) k_tiles(Buffers B) {
-    __shared__ uint32_t s_warp[kThreads / 32];
-    __shared__ bool s_last;
-    Ctl* ctl = B.ctl;
-    pdl_wait();
-    if (ld_volatile(&ctl->err)) return;
-    const uint32_t n = ctl->n_cells;
+// tiles_pass: tsum[t] = agents in cell tile t (8192 cells), for the tiles
+// bid, bid + nb, ...
+__device__ __forceinline__ void tiles_pass(Buffers& B, uint32_t bid, uint32_t nb, uint32_t* s_warp) {
+    const uint32_t n = B.ctl->n_cells;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (uint32_t tile = bid; tile < ntiles; tile += nb) {
         const uint4* src = reinterpret_cast<const uint4*>(B.cnt + tile * kScanTile + threadIdx.x * kScanV);
         uint32_t sum = 0;
 #pragma unroll
@@ -382,6 +375,19 @@ __global__ void __launch_bounds__(kThreads) k_tiles(Buffers B) {
         block_exclusive_scan(sum, s_warp, &total);
         if (threadIdx.x == 0) B.tsum[tile] = total;
     }
+}
+
+// k_tiles: the tile sums; the last block to finish turns them into exclusive
+// tile prefixes and writes the total and the sorted-agent count.
+__global__ void __launch_bounds__(kThreads) k_tiles(Buffers B) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    __shared__ bool s_last;
+    Ctl* ctl = B.ctl;
+    pdl_wait();
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t n = ctl->n_cells;
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+    tiles_pass(B, blockIdx.x, gridDim.x, s_warp);
     pdl_trigger();
     __threadfence();
     __syncthreads();
@@ -404,8 +410,39 @@ __global__ void __launch_bounds__(kThreads) k_tiles(Buffers B) {
     }
 }
 
-// k_scan: start[c] = tile prefix + prefix of the tile's own counts; the
-// counts are reset to zero for the next step.
+// One scan tile: start[c] = prefix (agents in the tiles before) + the tile's
+// own exclusive prefix; its counts are reset to zero for the next step.
+__device__ __forceinline__ void scan_tile(Buffers& B, uint32_t tile, uint32_t prefix, uint32_t* s_warp) {
+    const uint32_t base = tile * kScanTile + threadIdx.x * kScanV;
+    uint32_t v[kScanV];
+    uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
+#pragma unroll
+    for (int k = 0; k < kScanV / 4; k++) {
+        const uint4 u = src[k];
+        v[4 * k] = u.x;
+        v[4 * k + 1] = u.y;
+        v[4 * k + 2] = u.z;
+        v[4 * k + 3] = u.w;
+        src[k] = make_uint4(0, 0, 0, 0);
+    }
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanV; k++) tsum += v[k];
+    uint32_t total;
+    uint32_t run = prefix + block_exclusive_scan(tsum, s_warp, &total);
+    uint4* dst = reinterpret_cast<uint4*>(B.start + base);
+#pragma unroll
+    for (int k = 0; k < kScanV / 4; k++) {
+        uint4 o;
+        o.x = run; run += v[4 * k];
+        o.y = run; run += v[4 * k + 1];
+        o.z = run; run += v[4 * k + 2];
+        o.w = run; run += v[4 * k + 3];
+        dst[k] = o;
+    }
+}
+
+// k_scan: every tile with the prefixes k_tiles left in tsum.
 __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     __shared__ uint32_t s_warp[kThreads / 32];
     Ctl* ctl = B.ctl;
@@ -414,33 +451,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     const uint32_t n = ctl->n_cells;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t base = tile * kScanTile + threadIdx.x * kScanV;
-        uint32_t v[kScanV];
-        uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
-#pragma unroll
-        for (int k = 0; k < kScanV / 4; k++) {
-            const uint4 u = src[k];
-            v[4 * k] = u.x;
-            v[4 * k + 1] = u.y;
-            v[4 * k + 2] = u.z;
-            v[4 * k + 3] = u.w;
-            src[k] = make_uint4(0, 0, 0, 0);
-        }
-        uint32_t tsum = 0;
-#pragma unroll
-        for (int k = 0; k < kScanV; k++) tsum += v[k];
-        uint32_t total;
-        uint32_t run = B.tsum[tile] + block_exclusive_scan(tsum, s_warp, &total);
-        uint4* dst = reinterpret_cast<uint4*>(B.start + base);
-#pragma unroll
-        for (int k = 0; k < kScanV / 4; k++) {
-            uint4 o;
-            o.x = run; run += v[4 * k];
-            o.y = run; run += v[4 * k + 1];
-            o.z = run; run += v[4 * k + 2];
-            o.w = run; run += v[4 * k + 3];
-            dst[k] = o;
-        }
+        scan_tile(B, tile, B.tsum[tile], s_warp);
         if (tile == ntiles - 1 && threadIdx.x == 0) B.start[n] = B.tsum[ntiles];  // cells past n are empty
     }
     pdl_trigger();
@@ -452,15 +463,13 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
 // issuing all loads before the dependent start[] gathers.
 constexpr int kScatterILP = 4;
 
-__global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
+__device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
-    pdl_wait();
-    if (ld_volatile(&ctl->err)) return;
     const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
     const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_props = 0;  // k_move has consumed the old list
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < total; j0 += kScatterILP * stride) {
+    if (bid == 0 && threadIdx.x == 0) ctl->n_props = 0;  // the move pass has consumed the old list
+    const uint32_t stride = nb * blockDim.x;
+    for (uint32_t j0 = bid * blockDim.x + threadIdx.x; j0 < total; j0 += kScatterILP * stride) {
         uint64_t kr[kScatterILP];
         int4 p[kScatterILP];
         uint32_t id[kScatterILP], par[kScatterILP];
@@ -499,6 +508,12 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
             if (meta & M_BOUND) B.apar[nxt][dest[u]] = par[u];
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
+    pdl_wait();
+    if (ld_volatile(&B.ctl->err)) return;
+    scatter_pass(B, blockIdx.x, gridDim.x);
     pdl_trigger();
 }
 
@@ -551,61 +566,66 @@ __device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida
 // range of the cell-sorted array -- keeps the nearest eligible partner by
 // (dist^2, id) and claims it with atomicMin.  Any partner within a contact
 // radius lies inside that box, so the result equals the 27-cell search.
-__global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
-    extern __shared__ uint32_t s_list[];  // B.propose_chunk entries
-    __shared__ uint32_t s_n;
-    Ctl* ctl = B.ctl;
-    pdl_wait();
-    if (ld_volatile(&ctl->err)) return;
-    const uint32_t nxt = ctl->cur ^ 1u;
-    const uint32_t n = ctl->n_sorted;
+// One chunk of sorted agents [base, base + chunk): its free agents of
+// proposing species are compacted into s_list, then each searches its box.
+__device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_t n, uint32_t* s_list,
+                                              uint32_t* s_n) {
+    const uint32_t nxt = B.ctl->cur ^ 1u;
     const int4* __restrict__ pm = B.pm[nxt];
     const uint32_t* __restrict__ aid = B.aid[nxt];
     const uint32_t* __restrict__ start = B.start;
     const int lane = threadIdx.x & 31;
     const uint32_t chunk = B.propose_chunk;
-    for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk) {
-        if (threadIdx.x == 0) s_n = 0;
-        __syncthreads();
-        // compact the chunk's free agents of proposing species into s_list
-        for (uint32_t u = 0; u < chunk / kThreads; u++) {
-            const uint32_t i = base + u * kThreads + threadIdx.x;
-            const bool isp = i < n && B.pflag[i];
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isp);
-            uint32_t pos = 0;
-            if (lane == 0 && bal) pos = atomicAdd(&s_n, (uint32_t)__popc(bal));
-            pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
-            if (isp) s_list[pos + __popc(bal & ((1u << lane) - 1u))] = i;
-        }
-        __syncthreads();
-        const uint32_t np = s_n;
-        for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
-            const uint32_t gi = s_list[k];
-            const int4 p = pm[gi];
-            const uint32_t meta = (uint32_t)p.w;
-            const SimDev& S = B.sims[sim_of(meta)];
-            if (S.step >= S.max_step) continue;  // frozen simulation
-            const ModelDev& Mo = B.models[S.model];
-            const uint32_t sp = meta & M_SP;
-            const uint64_t mask = Mo.sp[sp].partner_mask;
-            const int rmax = Mo.sp[sp].rmax;
-            const int g = (int)S.g, sh = (int)S.shift;
-            const int xlo = max((p.x - rmax) >> sh, 0), xhi = min((p.x + rmax) >> sh, g - 1);
-            const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
-            const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
-            Best best;
-            uint32_t ida = kNone;
-            for (int zz = zlo; zz <= zhi; zz++)
-                for (int yy = ylo; yy <= yhi; yy++) {
-                    const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
-                    const uint32_t j1 = start[row + xhi + 1];
-                    for (uint32_t j = start[row + xlo]; j < j1; j++)
-                        if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
-                }
-            claim(B, best, ida, gi);
-        }
-        __syncthreads();
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
+    for (uint32_t u = 0; u < chunk / kThreads; u++) {
+        const uint32_t i = base + u * kThreads + threadIdx.x;
+        const bool isp = i < n && B.pflag[i];
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isp);
+        uint32_t pos = 0;
+        if (lane == 0 && bal) pos = atomicAdd(s_n, (uint32_t)__popc(bal));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+        if (isp) s_list[pos + __popc(bal & ((1u << lane) - 1u))] = i;
     }
+    __syncthreads();
+    const uint32_t np = *s_n;
+    for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
+        const uint32_t gi = s_list[k];
+        const int4 p = pm[gi];
+        const uint32_t meta = (uint32_t)p.w;
+        const SimDev& S = B.sims[sim_of(meta)];
+        if (S.step >= S.max_step) continue;  // frozen simulation
+        const ModelDev& Mo = B.models[S.model];
+        const uint32_t sp = meta & M_SP;
+        const uint64_t mask = Mo.sp[sp].partner_mask;
+        const int rmax = Mo.sp[sp].rmax;
+        const int g = (int)S.g, sh = (int)S.shift;
+        const int xlo = max((p.x - rmax) >> sh, 0), xhi = min((p.x + rmax) >> sh, g - 1);
+        const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
+        const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
+        Best best;
+        uint32_t ida = kNone;
+        for (int zz = zlo; zz <= zhi; zz++)
+            for (int yy = ylo; yy <= yhi; yy++) {
+                const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
+                const uint32_t j1 = start[row + xhi + 1];
+                for (uint32_t j = start[row + xlo]; j < j1; j++)
+                    if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
+            }
+        claim(B, best, ida, gi);
+    }
+    __syncthreads();  // s_list and s_n are reused by the next chunk
+}
+
+__global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
+    extern __shared__ uint32_t s_list[];  // B.propose_chunk entries
+    __shared__ uint32_t s_n;
+    pdl_wait();
+    if (ld_volatile(&B.ctl->err)) return;
+    const uint32_t n = B.ctl->n_sorted;
+    const uint32_t chunk = B.propose_chunk;
+    for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk)
+        propose_chunk(B, base, n, s_list, &s_n);
     pdl_trigger();
 }
 
@@ -691,17 +711,14 @@ __device__ void finalize_block(Buffers& B) {
 // i's id and nobody proposed to i.  Final edges are disjoint, so each is
 // applied without further synchronisation.  The last block to finish runs
 // the births and the step's bookkeeping.
-__global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
-    __shared__ bool s_last;
+__device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
-    pdl_wait();
-    if (ld_volatile(&ctl->err)) return;
     const uint32_t nxt = ctl->cur ^ 1u;
     const uint32_t np = ctl->n_props;
     int4* __restrict__ pm = B.pm[nxt];
     uint32_t* __restrict__ aid = B.aid[nxt];
     uint32_t* __restrict__ apar = B.apar[nxt];
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+    for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += nb * blockDim.x) {
         const uint2 e = B.props[k];
         const uint32_t i = e.x, j = e.y;
         const uint64_t kb = B.acc[j];
@@ -729,6 +746,14 @@ __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
         *wa = ma;
         *wb = mb;
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
+    __shared__ bool s_last;
+    Ctl* ctl = B.ctl;
+    pdl_wait();
+    if (ld_volatile(&ctl->err)) return;
+    accept_pass(B, blockIdx.x, gridDim.x);
     pdl_trigger();
     // last-block-done: every block's writes are visible to the last one
     __threadfence();

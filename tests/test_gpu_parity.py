@@ -79,6 +79,18 @@ def test_toy_full_length(A, oracle_mod):
     assert c[2] > 100                                          # C formed
 
 
+def test_toy_one_launch_of_all_steps(A, oracle_mod):
+    """All 200 steps in one abm_step call (25 replays of the 8-step graph)."""
+    g = A.Sim(W.toy(), W.TOY_SEED)
+    o = oracle_mod.OracleSim(W.toy(), W.TOY_SEED)
+    g.step(W.TOY_STEPS)
+    o.step(W.TOY_STEPS)
+    assert g.t == W.TOY_STEPS and g.digest() == o.digest()
+    assert_same_dump(g.dump(), o.dump(), "step 200")
+    g.close()
+    o.close()
+
+
 def test_mapk_scaled_parity(A, oracle_mod):
     c = _lockstep(A, oracle_mod, W.mapk(30_000), W.MAPK_SEED, 400, dump_every=100, digest_every=4)
     assert c[9:-1].sum() > 0                                  # complexes present
@@ -332,3 +344,4 @@ def test_restore_rejects_inconsistent_records(A):
         bad = np.delete(rec, hid[0])                      # a complex without its hidden partner
         with pytest.raises(A.AbmError):
             A.Sim(m, 3, restore=(bad, t, next_id))
+
