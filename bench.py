@@ -29,7 +29,7 @@ UNIT = "molecule-steps/s"
 # per-kernel bytes each launch must move per unit (agent or cell) in this
 # design; the step as a whole must read and rewrite the 20-byte agent record
 STEP_BYTES_PER_AGENT = 40
-KERNEL_BYTES = {"k_move": (44, "agent"), "k_tiles": (4, "cell"), "k_scan": (12, "cell"),
+KERNEL_BYTES = {"k_move": (44, "agent"), "k_tile_prefix": (8 / 8192, "cell"), "k_scan": (12, "cell"),
                 "k_scatter": (56, "agent"), "k_propose": (24, "agent"), "k_accept": (4, "agent")}
 
 
@@ -145,14 +145,21 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "engine.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_14603_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if the
-    kernel source is unchanged since the capture (else None)."""
-    import hashlib
+    kernel sources (kernels.cu + engine.cuh) are unchanged since the capture
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    src = os.path.join(ROOT, "paper_2606_14603_b300", "csrc", "kernels.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha()
         for line in open(path):
             f = line.split()
             if len(f) >= 5 and not line.startswith("#") and f[0] == kernel and f[1] == sha:

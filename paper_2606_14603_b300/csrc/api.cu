@@ -243,7 +243,8 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
         16 * E, 4 * E, 8 * E,                  // extras
         16 * (size_t)Bc, 4 * (size_t)Bc,       // births
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
-        4 * tiles,                             // tile sums / prefixes
+        4 * kTileStride * tiles,               // tile counts (one per 128-byte line)
+        4 * tiles,                             // tile prefixes
         sizeof(SimDev) * S, sizeof(ModelDev) * S,
         8 * (size_t)S * 512, 8 * (size_t)S,    // counts, digests
         sizeof(MonDev) * S, 4 * (size_t)S * 512,   // threshold monitors, their weights
@@ -523,6 +524,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.bpar = (uint32_t*)at();
     B.cnt = (uint32_t*)at();
     B.start = (uint32_t*)at();
+    B.tcnt = (uint32_t*)at();
     B.tsum = (uint32_t*)at();
     B.sims = (SimDev*)at();
     B.models = (ModelDev*)at();
@@ -563,6 +565,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
         (int)std::max<uint64_t>(1, std::min<uint64_t>((b->cap_agents + chunk - 1) / chunk, (uint64_t)sms * 32));
     b->L.blocks_scan = (int)std::max<uint64_t>(1, std::min<uint64_t>(B.n_tiles_max, (uint64_t)sms * 4));
     b->L.blocks_accept = sms;
+    b->L.prefix_kernel = B.n_tiles_max > kDirectTiles;
 
     std::vector<int16_t> table(65536);
     if (o->ncdf_table) std::memcpy(table.data(), o->ncdf_table, 2 * 65536);
@@ -1220,7 +1223,7 @@ abm_status abm_profile_step(abm_sim* s, uint32_t n, float* kernel_ms, uint32_t n
     return s ? abm_batch_profile_step(s->b, n, kernel_ms, n_kernels) : ABM_EINVAL;
 }
 const char* abm_kernel_name(uint32_t k) {
-    static const char* names[] = {"k_move", "k_tiles", "k_scan", "k_scatter", "k_propose", "k_accept"};
+    static const char* names[] = {"k_move", "k_tile_prefix", "k_scan", "k_scatter", "k_propose", "k_accept"};
     return k < (uint32_t)kStepKernels ? names[k] : nullptr;
 }
 abm_status abm_step_index(abm_sim* s, uint32_t* out) {

@@ -11,7 +11,10 @@
 //   xpm/xid/xkr  released partners appended by the move pass (C/2 + 1)
 //   bpm/bpar     births of the step (B)
 //   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
-//   tsum[T+1]    per-tile cell sums, then exclusive tile prefixes
+//   tcnt[T]      agents per cell tile (8192 cells), counted by the move pass,
+//                one counter per 128-byte line (kTileStride words apart) so
+//                that the atomics of different tiles meet in different L2 lines
+//   tsum[T+1]    exclusive tile prefixes (grids of more than kDirectTiles tiles)
 //   sims[S], models[S], obs (counts/digests), ctl
 //
 // meta word: bits 0-5 species, 6-7 compartment, 8 carrier, 9 carrier is
@@ -30,6 +33,8 @@ constexpr int kMaxComp = 4;
 constexpr int kMaxSims = 2048;
 constexpr uint32_t kMaxBirths = 8192;
 constexpr int kScanTile = 8192;           // cells per scan tile (256 threads x 32)
+constexpr int kTileStride = 32;           // words between two tile counters
+constexpr uint32_t kDirectTiles = 8192;   // up to this many tiles, each scan block adds up its own prefix
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kMonTrace = 1024;      // evaluations kept per threshold monitor
 constexpr uint64_t kEmpty = 0xFFFFFFFFFFFFFFFFull;
@@ -125,7 +130,7 @@ struct Ctl {
     uint32_t n_births;       // births of this step
     uint32_t cur;            // current buffer
     uint32_t n_cells;        // cells in use
-    uint32_t scan_ticket;    // blocks of k_tiles finished this step
+    uint32_t pad0;
     uint32_t epoch;          // global step counter (look-back tags)
     uint32_t err;
     uint32_t err_info;
@@ -152,6 +157,7 @@ struct Buffers {
     uint32_t* bpar;
     uint32_t* cnt;
     uint32_t* start;
+    uint32_t* tcnt;
     uint32_t* tsum;
     SimDev* sims;
     ModelDev* models;
@@ -276,6 +282,7 @@ struct Launch {
     int blocks_scan;
     int blocks_accept;       // CTAs of the acceptance kernel (walks the proposal list)
     int blocks_propose;      // CTAs of the proposal search, one chunk of sorted agents each
+    bool prefix_kernel;      // more than kDirectTiles tiles: tile prefixes by k_tile_prefix
 };
 
 // CTAs of k_move that fit on one SM at once (its registers decide).

@@ -6,8 +6,10 @@
 // control block so that a captured CUDA graph replays them unchanged:
 //
 //   k_move      P1 events + P2 Brownian move + cell key + histogram rank
-//   k_tiles     per-tile sums of the cell histogram, then tile prefixes
-//   k_scan      exclusive scan of the cell histogram within each tile
+//               (and agents per tile of 8192 cells)
+//   k_tile_prefix  prefixes of the per-tile agent counts (grids of more
+//               than 8192 tiles only)
+//   k_scan      exclusive scan of the cell histogram, tile prefixes included
 //   k_scatter   reorder every live agent by cell into the other buffer
 //   k_propose   neighbour query over the cells a contact radius can reach,
 //               nearest eligible partner, atomicMin on a packed key
@@ -184,6 +186,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, ui
                 if (k < B.cap_extras) {
                     const uint32_t key = cell_of(S, q.x, q.y, q.z);
                     const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
+                    atomicAdd(&B.tcnt[key / kScanTile * kTileStride], 1u);
                     B.xpm[k] = q;
                     B.xid[k] = par;
                     B.xkr[k] = (uint64_t)key << 32 | rank;
@@ -279,10 +282,7 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
     const uint32_t n = ctl->n_in;
-    if (bid == 0 && threadIdx.x == 0) {
-        ctl->scan_ticket = 0;
-        ctl->n_sorted = 0;  // the scan's last tile writes the real count
-    }
+    if (bid == 0 && threadIdx.x == 0) ctl->n_sorted = 0;  // the scan writes the real count
     const int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
     const uint32_t* __restrict__ apar = B.apar[cur];
@@ -291,37 +291,62 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     const uint32_t stride = nb * blockDim.x;
     for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
     // threshold monitors add up the records as they stand after t steps (a
-    // loop of its own: it keeps the main loop's register count; the main loop
-    // then finds these records in L1)
+    // loop of its own: it keeps the main loop's register count)
     if (ctl->n_monitors)
         for (uint32_t i = bid * blockDim.x + threadIdx.x; i < n; i += stride)
             monitor_record(B, (uint32_t)pm[i].w, kNone);
-    // one agent per iteration; the next agent's record is loaded while this
-    // one runs its chain of dependent table lookups and the histogram atomic
-    uint32_t i = bid * blockDim.x + threadIdx.x;
+    // Each warp takes a contiguous range of agents, 32 consecutive ones per
+    // iteration (coalesced).  The next 32 records are loaded while these run
+    // their chain of dependent table lookups and the histogram atomic.  The
+    // range is in cell order from the last step, so its agents stay in one
+    // cell tile for long stretches: the warp keeps the tile's count in
+    // registers and adds it to the tile counter when the tile changes.
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = nb * (blockDim.x >> 5);
+    const uint32_t w = bid * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t len = ((n + warps - 1) / warps + 31u) & ~31u;
+    const uint32_t wbeg = min(n, w * len), wend = min(n, wbeg + len);
     int4 nx_p = make_int4(0, 0, 0, 0);
     uint32_t nx_id = 0, nx_par = 0;
-    if (i < n) {
-        nx_p = pm[i];
-        nx_id = aid[i];
-        nx_par = apar[i];
+    if (wbeg + lane < wend) {
+        nx_p = pm[wbeg + lane];
+        nx_id = aid[wbeg + lane];
+        nx_par = apar[wbeg + lane];
     }
-    for (; i < n; i += stride) {
+    uint32_t run_tile = kNone, run_n = 0;  // the same in every lane
+    for (uint32_t base = wbeg; base < wend; base += 32) {  // uniform over the warp
+        const uint32_t i = base + lane;
         MoveState a;
+        a.flags = 0;
         a.p = nx_p;
         a.id = nx_id;
         const uint32_t par = nx_par;
-        const uint32_t j = i + stride;
-        if (j < n) {
-            nx_p = pm[j];
-            nx_id = aid[j];
-            nx_par = apar[j];
+        if (i + 32 < wend) {
+            nx_p = pm[i + 32];
+            nx_id = aid[i + 32];
+            nx_par = apar[i + 32];
         }
-        move_phase1(B, ctl, i, par, a);
-        move_phase2(a);
+        if (i < wend) {
+            move_phase1(B, ctl, i, par, a);
+            move_phase2(a);
+        }
         const uint32_t rank = (a.flags & 1u) ? atomicAdd(&B.cnt[a.key], 1u) : 0u;
-        move_phase4(B, ctl, cur, i, a, rank);
+        const uint32_t tile = (a.flags & 1u) ? a.key / kScanTile : kNone;
+        const uint32_t live = __ballot_sync(0xFFFFFFFFu, tile != kNone);
+        if (live) {
+            const uint32_t t0 = __shfl_sync(0xFFFFFFFFu, tile, __ffs(live) - 1);
+            const uint32_t same = __ballot_sync(0xFFFFFFFFu, tile == t0);
+            if (t0 != run_tile) {
+                if (run_n && lane == 0) atomicAdd(&B.tcnt[run_tile * kTileStride], run_n);
+                run_tile = t0;
+                run_n = 0;
+            }
+            run_n += __popc(same);
+            if (tile != kNone && tile != t0) atomicAdd(&B.tcnt[tile * kTileStride], 1u);
+        }
+        if (i < wend) move_phase4(B, ctl, cur, i, a, rank);
     }
+    if (run_n && lane == 0) atomicAdd(&B.tcnt[run_tile * kTileStride], run_n);
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_move(Buffers B) {
@@ -357,57 +382,42 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 }
 
 // ------------------------------------------------------------------------
-// The cell scan in two passes with no waiting between blocks.
-// tiles_pass: tsum[t] = agents in cell tile t (8192 cells), for the tiles
-// bid, bid + nb, ...
-__device__ __forceinline__ void tiles_pass(Buffers& B, uint32_t bid, uint32_t nb, uint32_t* s_warp) {
-    const uint32_t n = B.ctl->n_cells;
-    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    for (uint32_t tile = bid; tile < ntiles; tile += nb) {
-        const uint4* src = reinterpret_cast<const uint4*>(B.cnt + tile * kScanTile + threadIdx.x * kScanV);
-        uint32_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < kScanV / 4; k++) {
-            const uint4 u = src[k];
-            sum += u.x + u.y + u.z + u.w;
-        }
-        uint32_t total;
-        block_exclusive_scan(sum, s_warp, &total);
-        if (threadIdx.x == 0) B.tsum[tile] = total;
-    }
-}
-
-// k_tiles: the tile sums; the last block to finish turns them into exclusive
-// tile prefixes and writes the total and the sorted-agent count.
-__global__ void __launch_bounds__(kThreads) k_tiles(Buffers B) {
-    __shared__ uint32_t s_warp[kThreads / 32];
-    __shared__ bool s_last;
+// The cell scan.  The move pass has counted the agents of every cell and of
+// every tile of 8192 cells.  Up to kDirectTiles tiles, each k_scan block
+// adds up the tile counts before its own range of tiles itself; beyond that
+// one block of k_tile_prefix first turns the tile counts into prefixes.
+__global__ void __launch_bounds__(1024) k_tile_prefix(Buffers B) {
+    __shared__ uint32_t s_warp[32];
     Ctl* ctl = B.ctl;
     pdl_wait();
     if (ld_volatile(&ctl->err)) return;
     const uint32_t n = ctl->n_cells;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    tiles_pass(B, blockIdx.x, gridDim.x, s_warp);
-    pdl_trigger();
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&ctl->scan_ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t run = 0;
     for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
         const uint32_t t = base + threadIdx.x;
-        const uint32_t v = t < ntiles ? ld_volatile(&B.tsum[t]) : 0u;
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan(v, s_warp, &total);
-        if (t < ntiles) B.tsum[t] = run + ex;
-        run += total;
+        const uint32_t v = t < ntiles ? B.tcnt[t * kTileStride] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t wpre = 0, tot = 0;
+        for (int k = 0; k < (int)(blockDim.x / 32); k++) {
+            const uint32_t sw = s_warp[k];
+            if (k < warp) wpre += sw;
+            tot += sw;
+        }
+        __syncthreads();
+        if (t < ntiles) B.tsum[t] = run + wpre + incl - v;
+        run += tot;
     }
-    if (threadIdx.x == 0) {
-        B.tsum[ntiles] = run;
-        ctl->n_sorted = run;
-    }
+    if (threadIdx.x == 0) B.tsum[ntiles] = run;
+    pdl_trigger();
 }
 
 // One scan tile: start[c] = prefix (agents in the tiles before) + the tile's
@@ -442,7 +452,9 @@ __device__ __forceinline__ void scan_tile(Buffers& B, uint32_t tile, uint32_t pr
     }
 }
 
-// k_scan: every tile with the prefixes k_tiles left in tsum.
+// k_scan: block b scans a contiguous range of tiles; the agents before the
+// range come from the tile counts (or from k_tile_prefix on large grids).
+// The block with the last tile writes the total and the sorted-agent count.
 __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     __shared__ uint32_t s_warp[kThreads / 32];
     Ctl* ctl = B.ctl;
@@ -450,9 +462,28 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     if (ld_volatile(&ctl->err)) return;
     const uint32_t n = ctl->n_cells;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        scan_tile(B, tile, B.tsum[tile], s_warp);
-        if (tile == ntiles - 1 && threadIdx.x == 0) B.start[n] = B.tsum[ntiles];  // cells past n are empty
+    const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const uint32_t t0 = min(ntiles, blockIdx.x * per), t1 = min(ntiles, t0 + per);
+    if (t0 < t1) {
+        uint32_t before;
+        if (ntiles <= kDirectTiles) {
+            uint32_t v = 0;
+            for (uint32_t t = threadIdx.x; t < t0; t += blockDim.x) v += B.tcnt[t * kTileStride];
+            uint32_t total;
+            block_exclusive_scan(v, s_warp, &total);
+            before = total;
+        } else {
+            before = B.tsum[t0];
+        }
+        for (uint32_t t = t0; t < t1; t++) {
+            const uint32_t own = B.tcnt[t * kTileStride];
+            scan_tile(B, t, before, s_warp);
+            before += own;
+        }
+        if (t1 == ntiles && threadIdx.x == 0) {
+            B.start[n] = before;  // cells past n are empty
+            ctl->n_sorted = before;
+        }
     }
     pdl_trigger();
 }
@@ -468,6 +499,9 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
     const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
     const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
     if (bid == 0 && threadIdx.x == 0) ctl->n_props = 0;  // the move pass has consumed the old list
+    // the scan has read this step's tile counts: zero them for the next step
+    const uint32_t ntiles = (ctl->n_cells + kScanTile - 1) / kScanTile;
+    for (uint32_t t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) B.tcnt[t * kTileStride] = 0;
     const uint32_t stride = nb * blockDim.x;
     for (uint32_t j0 = bid * blockDim.x + threadIdx.x; j0 < total; j0 += kScatterILP * stride) {
         uint64_t kr[kScatterILP];
@@ -959,10 +993,11 @@ __global__ void k_debug_philox(const uint4* ctr, const uint2* key, uint4* out, s
 // launching while the previous kernel in the stream drains (it waits in
 // pdl_wait before touching any data).
 template <typename Kernel>
-cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B, size_t smem = 0) {
+cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B, size_t smem = 0,
+                       int threads = kThreads) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -981,7 +1016,7 @@ int move_blocks_per_sm() {
 
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s) {
     cudaError_t e = launch_pdl(k_move, L.blocks_agents, s, B);
-    if (e == cudaSuccess) e = launch_pdl(k_tiles, L.blocks_scan, s, B);
+    if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_scatter, L.blocks_agents, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, 4 * (size_t)B.propose_chunk);
@@ -993,7 +1028,7 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
     cudaEventRecord(ev[0], s);
     k_move<<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[1], s);
-    k_tiles<<<L.blocks_scan, kThreads, 0, s>>>(B);
+    if (L.prefix_kernel) k_tile_prefix<<<1, 1024, 0, s>>>(B);
     cudaEventRecord(ev[2], s);
     k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[3], s);

@@ -345,3 +345,19 @@ def test_restore_rejects_inconsistent_records(A):
         with pytest.raises(A.AbmError):
             A.Sim(m, 3, restore=(bad, t, next_id))
 
+
+
+def test_large_grid_takes_the_tile_prefix_kernel(A, oracle_mod):
+    """A batch whose grid exceeds 8192 scan tiles (67M cells) computes the tile
+    prefixes in k_tile_prefix instead of inside the scan: same results."""
+    m = W.toy(700, 600, edge_um=0.5)
+    b = A.Batch(200_000, 8193 * 8192, 2)
+    s = b.add(m, 9)
+    o = oracle_mod.OracleSim(m, 9)
+    for t in range(4):
+        b.step(10)
+        o.step(10)
+        assert b.digest(s) == o.digest(), f"step {10 * (t + 1)}"
+    assert_same_dump(b.dump(s), o.dump(), "step 40")
+    assert b.profile_step(1)["k_tile_prefix"] > 0
+    b.close()
