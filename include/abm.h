@@ -298,7 +298,9 @@ abm_status  abm_dump_noalloc(abm_sim* sim, abm_record* out, size_t cap, size_t* 
 /* Runs n steps without the CUDA graph, with a CUDA event on the stream
  * before and after each of the step's kernels, and writes the summed time of
  * each kernel in milliseconds to kernel_ms[0..5] (n_kernels >= 6; names from
- * abm_kernel_name).  Synchronous.  The state advances exactly as abm_step. */
+ * abm_kernel_name; slot 1, k_tile_prefix, runs only on grids of more than
+ * 8192 tiles of 8192 cells and reads 0 otherwise).  Synchronous.  The state
+ * advances exactly as abm_step. */
 abm_status  abm_profile_step(abm_sim* sim, uint32_t n, float* kernel_ms, uint32_t n_kernels);
 abm_status  abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, uint32_t n_kernels);
 /* Name of step kernel k (0..5), or NULL. */

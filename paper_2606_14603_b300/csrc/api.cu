@@ -968,7 +968,7 @@ abm_status abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, ui
         for (int k = 0; k < kStepKernels && e == cudaSuccess; k++) {
             float ms = 0;
             e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-            acc[k] += ms;
+            if (k != 1 || b->L.prefix_kernel) acc[k] += ms;  // slot 1: k_tile_prefix, large grids only
         }
     }
     for (int k = 0; k <= kStepKernels; k++) cudaEventDestroy(ev[k]);

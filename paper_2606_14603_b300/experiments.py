@@ -1,6 +1,6 @@
 """Volume invariance of the dose readout, and runtime against volume.
 
-Sec. 3 (runtime discussion): at fixed concentrations the number of
+Sec. 3.2 (simulation performance factors): at fixed concentrations the number of
 molecule-agents grows in proportion to the simulated volume, the work per
 agent stays about the same, so the cost of a step grows about linearly with
 volume; and the biological readout, the final relative change of pERK + ppERK
