@@ -131,15 +131,15 @@ struct Ctl {
     uint32_t cur;            // current buffer
     uint32_t n_cells;        // cells in use
     uint32_t pad0;
-    uint32_t epoch;          // global step counter
+    uint32_t epoch;          // global step counter (look-back tags)
     uint32_t err;
     uint32_t err_info;
     uint32_t n_sims;         // sim slots in use (upper bound of the table)
     uint32_t dump_n;
     uint32_t n_monitors;     // simulations with an active threshold monitor
-    uint32_t n_next;         // agents of the next step (sorted + births)
-    uint32_t nxt;            // buffer the scatter wrote this step
+    uint32_t blocks_done;    // blocks of k_accept finished this step
     uint32_t n_props;        // proposals of this step (list in props)
+    uint32_t pad;
 };
 
 struct Buffers {

@@ -357,102 +357,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_move(Buffers B) {
 }
 
 // ------------------------------------------------------------------------
-// Exclusive block scan of one 64-bit value per thread (two 32-bit sums
-// carried side by side); returns the thread's exclusive prefix and writes
-// the block total to *total.
-__device__ __forceinline__ uint64_t block_exclusive_scan64(uint64_t v, uint64_t* s_warp, uint64_t* total) {
+// Exclusive block scan of one value per thread; returns the thread's
+// exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t incl = v;
+    uint32_t incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += y;
     }
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    uint64_t wpre = 0, tot = 0;
+    uint32_t wpre = 0, tot = 0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; w++) {
-        const uint64_t sw = s_warp[w];
+        const uint32_t sw = s_warp[w];
         if (w < warp) wpre += sw;
         tot += sw;
     }
-    __syncthreads();
+    __syncthreads();  // s_warp may be reused by the caller
     *total = tot;
     return wpre + incl - v;
-}
-
-// ------------------------------------------------------------------------
-// Births, run by one block of k_scan once the number of sorted agents ns is
-// known: newborns get ids next_id + rank, the rank ordering the births of
-// the same simulation by parent id, and are written after the sorted agents
-// (slots the scatter does not touch).  The same block evaluates threshold
-// monitors (k_move has added up the state this step started from) and
-// leaves the next step's agent count; k_accept flips the buffers.
-constexpr int kKeyTile = 1024;
-
-__device__ void births_block(Buffers& B, uint32_t ns) {
-    __shared__ uint64_t s_key[kKeyTile];
-    Ctl* ctl = B.ctl;
-    const uint32_t nxt = ctl->cur ^ 1u;
-    uint32_t nb = ld_volatile(&ctl->n_births);
-    if (nb > B.cap_births) nb = B.cap_births;  // the overflow was already flagged
-    if (nb && (uint64_t)ns + nb > B.cap_agents) {
-        if (threadIdx.x == 0) raise_error(ctl, ERR_CAPACITY_AGENTS, ns + nb);
-        return;
-    }
-    // key of birth k: simulation in the high word, parent id in the low word
-    auto key_of = [&](uint32_t k) -> uint64_t {
-        return (uint64_t)(sim_of((uint32_t)B.bpm[k].w)) << 32 | B.bpar[k];
-    };
-    // rank of each birth among the births of its simulation (ids are unique:
-    // at most one birth per parent per step), and whether it is the last one
-    const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
-    constexpr int kMaxPer = (kMaxBirths + kThreads - 1) / kThreads;
-    uint32_t lt[kMaxPer], gt[kMaxPer];
-    uint64_t mine[kMaxPer];
-    for (uint32_t q = 0; q < per; q++) {
-        const uint32_t k = threadIdx.x + q * blockDim.x;
-        mine[q] = k < nb ? key_of(k) : 0;
-        lt[q] = gt[q] = 0;
-    }
-    for (uint32_t base = 0; base < nb; base += kKeyTile) {
-        const uint32_t m = min((uint32_t)kKeyTile, nb - base);
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) s_key[j] = key_of(base + j);
-        __syncthreads();
-        for (uint32_t q = 0; q < per; q++) {
-            const uint64_t key = mine[q];
-            for (uint32_t j = 0; j < m; j++) {
-                const uint64_t o = s_key[j];
-                const bool same = (o >> 32) == (key >> 32);
-                lt[q] += same & (o < key);
-                gt[q] += same & (o > key);
-            }
-        }
-    }
-    for (uint32_t q = 0; q < per; q++) {
-        const uint32_t k = threadIdx.x + q * blockDim.x;
-        if (k >= nb) continue;
-        const uint32_t s = (uint32_t)(mine[q] >> 32);
-        const uint64_t nid = (uint64_t)B.sims[s].next_id + lt[q];
-        if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
-        B.pm[nxt][ns + k] = B.bpm[k];
-        B.aid[nxt][ns + k] = (uint32_t)nid;
-    }
-    __syncthreads();
-    for (uint32_t q = 0; q < per; q++) {
-        const uint32_t k = threadIdx.x + q * blockDim.x;
-        if (k < nb && gt[q] == 0) B.sims[mine[q] >> 32].next_id += lt[q] + 1;  // one writer per sim
-    }
-    const uint32_t n_sims = ctl->n_sims;
-    if (ctl->n_monitors)
-        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x) monitor_eval(B, s);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ctl->n_next = ns + nb;
-        ctl->n_births = 0;
-    }
 }
 
 // ------------------------------------------------------------------------
@@ -494,14 +420,9 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(Buffers B) {
     pdl_trigger();
 }
 
-// One scan tile: start[c] = agents before the tile + the tile's own
-// exclusive prefix; its counts are reset to zero for the next step.  The
-// agents before the tile are `prefix` plus the sum over the block of pre_v,
-// added up in the same block scan as the tile's counts (high and low word),
-// so the loads of both are in flight together.  Returns the agents before
-// the next tile.
-__device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_t prefix, uint32_t pre_v,
-                                              uint64_t* s_warp) {
+// One scan tile: start[c] = prefix (agents in the tiles before) + the tile's
+// own exclusive prefix; its counts are reset to zero for the next step.
+__device__ __forceinline__ void scan_tile(Buffers& B, uint32_t tile, uint32_t prefix, uint32_t* s_warp) {
     const uint32_t base = tile * kScanTile + threadIdx.x * kScanV;
     uint32_t v[kScanV];
     uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
@@ -514,13 +435,11 @@ __device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_
         v[4 * k + 3] = u.w;
         src[k] = make_uint4(0, 0, 0, 0);
     }
-    uint32_t own = 0;
+    uint32_t tsum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanV; k++) own += v[k];
-    uint64_t total;
-    const uint64_t ex = block_exclusive_scan64((uint64_t)pre_v << 32 | own, s_warp, &total);
-    const uint32_t before = prefix + (uint32_t)(total >> 32);
-    uint32_t run = before + (uint32_t)ex;  // the low words never carry: a tile holds < 2^32 agents
+    for (int k = 0; k < kScanV; k++) tsum += v[k];
+    uint32_t total;
+    uint32_t run = prefix + block_exclusive_scan(tsum, s_warp, &total);
     uint4* dst = reinterpret_cast<uint4*>(B.start + base);
 #pragma unroll
     for (int k = 0; k < kScanV / 4; k++) {
@@ -531,15 +450,13 @@ __device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_
         o.w = run; run += v[4 * k + 3];
         dst[k] = o;
     }
-    return before + (uint32_t)total;
 }
 
 // k_scan: block b scans a contiguous range of tiles; the agents before the
 // range come from the tile counts (or from k_tile_prefix on large grids).
-// The block with the last tile knows the number of sorted agents: it writes
-// it, places this step's births after them and evaluates threshold monitors.
+// The block with the last tile writes the total and the sorted-agent count.
 __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
-    __shared__ uint64_t s_warp[kThreads / 32];
+    __shared__ uint32_t s_warp[kThreads / 32];
     Ctl* ctl = B.ctl;
     pdl_wait();
     if (ld_volatile(&ctl->err)) return;
@@ -547,25 +464,28 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
     const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
     const uint32_t t0 = min(ntiles, blockIdx.x * per), t1 = min(ntiles, t0 + per);
-    uint32_t before = 0;
     if (t0 < t1) {
-        uint32_t pre_v = 0;
+        uint32_t before;
         if (ntiles <= kDirectTiles) {
-            for (uint32_t t = threadIdx.x; t < t0; t += blockDim.x) pre_v += B.tcnt[t * kTileStride];
+            uint32_t v = 0;
+            for (uint32_t t = threadIdx.x; t < t0; t += blockDim.x) v += B.tcnt[t * kTileStride];
+            uint32_t total;
+            block_exclusive_scan(v, s_warp, &total);
+            before = total;
         } else {
             before = B.tsum[t0];
         }
-        for (uint32_t t = t0; t < t1; t++) before = scan_tile(B, t, before, t == t0 ? pre_v : 0u, s_warp);
-    }
-    pdl_trigger();
-    const bool last = ntiles ? (t0 < t1 && t1 == ntiles) : blockIdx.x == 0;
-    if (last) {
-        if (threadIdx.x == 0) {
+        for (uint32_t t = t0; t < t1; t++) {
+            const uint32_t own = B.tcnt[t * kTileStride];
+            scan_tile(B, t, before, s_warp);
+            before += own;
+        }
+        if (t1 == ntiles && threadIdx.x == 0) {
             B.start[n] = before;  // cells past n are empty
             ctl->n_sorted = before;
         }
-        births_block(B, before);
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------
@@ -578,10 +498,7 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
     const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
-    if (bid == 0 && threadIdx.x == 0) {
-        ctl->n_props = 0;  // the move pass has consumed the old list
-        ctl->nxt = nxt;    // the buffer k_accept works on
-    }
+    if (bid == 0 && threadIdx.x == 0) ctl->n_props = 0;  // the move pass has consumed the old list
     // the scan has read this step's tile counts: zero them for the next step
     const uint32_t ntiles = (ctl->n_cells + kScanTile - 1) / kScanTile;
     for (uint32_t t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) B.tcnt[t * kTileStride] = 0;
@@ -747,13 +664,90 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
 }
 
 // ------------------------------------------------------------------------
+// Births and per-step bookkeeping, run by the last block of k_accept:
+// newborns get ids next_id + rank, the rank ordering the births of the same
+// simulation by parent id, and are appended after the sorted agents; then
+// the buffer flips and every active simulation's step counter advances.
+constexpr int kKeyTile = 1024;
+
+__device__ void finalize_block(Buffers& B) {
+    __shared__ uint64_t s_key[kKeyTile];
+    Ctl* ctl = B.ctl;
+    const uint32_t nxt = ctl->cur ^ 1u;
+    const uint32_t ns = ctl->n_sorted;
+    uint32_t nb = ld_volatile(&ctl->n_births);
+    if (nb > B.cap_births) nb = B.cap_births;  // the overflow was already flagged
+    if (nb && (uint64_t)ns + nb > B.cap_agents) {
+        if (threadIdx.x == 0) raise_error(ctl, ERR_CAPACITY_AGENTS, ns + nb);
+        return;
+    }
+    // key of birth k: simulation in the high word, parent id in the low word
+    auto key_of = [&](uint32_t k) -> uint64_t {
+        return (uint64_t)(sim_of((uint32_t)B.bpm[k].w)) << 32 | B.bpar[k];
+    };
+    // rank of each birth among the births of its simulation (ids are unique:
+    // at most one birth per parent per step), and whether it is the last one
+    const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+    constexpr int kMaxPer = (kMaxBirths + kThreads - 1) / kThreads;
+    uint32_t lt[kMaxPer], gt[kMaxPer];
+    uint64_t mine[kMaxPer];
+    for (uint32_t q = 0; q < per; q++) {
+        const uint32_t k = threadIdx.x + q * blockDim.x;
+        mine[q] = k < nb ? key_of(k) : 0;
+        lt[q] = gt[q] = 0;
+    }
+    for (uint32_t base = 0; base < nb; base += kKeyTile) {
+        const uint32_t m = min((uint32_t)kKeyTile, nb - base);
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) s_key[j] = key_of(base + j);
+        __syncthreads();
+        for (uint32_t q = 0; q < per; q++) {
+            const uint64_t key = mine[q];
+            for (uint32_t j = 0; j < m; j++) {
+                const uint64_t o = s_key[j];
+                const bool same = (o >> 32) == (key >> 32);
+                lt[q] += same & (o < key);
+                gt[q] += same & (o > key);
+            }
+        }
+    }
+    for (uint32_t q = 0; q < per; q++) {
+        const uint32_t k = threadIdx.x + q * blockDim.x;
+        if (k >= nb) continue;
+        const uint32_t s = (uint32_t)(mine[q] >> 32);
+        const uint64_t nid = (uint64_t)B.sims[s].next_id + lt[q];
+        if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
+        B.pm[nxt][ns + k] = B.bpm[k];
+        B.aid[nxt][ns + k] = (uint32_t)nid;
+    }
+    __syncthreads();
+    for (uint32_t q = 0; q < per; q++) {
+        const uint32_t k = threadIdx.x + q * blockDim.x;
+        if (k < nb && gt[q] == 0) B.sims[mine[q] >> 32].next_id += lt[q] + 1;  // one writer per sim
+    }
+    const uint32_t n_sims = ctl->n_sims;
+    if (ctl->n_monitors)  // k_move added up the state this step started from
+        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x) monitor_eval(B, s);
+    for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
+        if (B.sims[s].active && B.sims[s].step < B.sims[s].max_step) B.sims[s].step += 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->n_in = ns + nb;
+        ctl->n_extra = 0;
+        ctl->n_births = 0;
+        ctl->cur = nxt;
+        ctl->epoch = ctl->epoch + 1;
+    }
+}
+
+// ------------------------------------------------------------------------
 // k_accept: walks the proposal list; edge i -> j is final iff j's slot holds
 // i's id and nobody proposed to i.  Final edges are disjoint, so each is
-// applied without further synchronisation.  Block 0 also advances the step
-// counters and flips the buffers for the next step.
+// applied without further synchronisation.  The last block to finish runs
+// the births and the step's bookkeeping.
 __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
-    const uint32_t nxt = ctl->nxt;  // block 0 flips ctl->cur meanwhile
+    const uint32_t nxt = ctl->cur ^ 1u;
     const uint32_t np = ctl->n_props;
     int4* __restrict__ pm = B.pm[nxt];
     uint32_t* __restrict__ aid = B.aid[nxt];
@@ -789,24 +783,21 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
 }
 
 __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
+    __shared__ bool s_last;
     Ctl* ctl = B.ctl;
     pdl_wait();
     if (ld_volatile(&ctl->err)) return;
-    if (blockIdx.x == 0) {
-        // the step's bookkeeping: no other block of this kernel reads these
-        // (they take the buffer index from ctl->nxt and no step counter)
-        const uint32_t n_sims = ctl->n_sims;
-        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
-            if (B.sims[s].active && B.sims[s].step < B.sims[s].max_step) B.sims[s].step += 1;
-        if (threadIdx.x == 0) {
-            ctl->n_in = ctl->n_next;
-            ctl->n_extra = 0;
-            ctl->cur = ctl->nxt;
-            ctl->epoch = ctl->epoch + 1;
-        }
-    }
     accept_pass(B, blockIdx.x, gridDim.x);
     pdl_trigger();
+    // last-block-done: every block's writes are visible to the last one
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    finalize_block(B);
+    if (threadIdx.x == 0) ctl->blocks_done = 0;
 }
 
 // ------------------------------------------------------------------------
