@@ -226,7 +226,39 @@ def cpu_baseline(model, seed, name, seconds=12.0):
             "sample": f"{name}: the first {steps} steps from t = 0, serial oracle, one thread"}
 
 
-def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0):
+def _sweep_oracle_task(args):
+    """One sweep simulation on the oracle (a worker process): molecule-steps
+    and seconds of `steps` steps from t = 0 (creation not timed)."""
+    k, steps, scale = args
+    import oracle
+    import workloads as W
+    model, seed = W.sweep(scale)[k]
+    sim = oracle.OracleSim(model, seed)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    el = time.perf_counter() - t0
+    sim.close()
+    return model.n_agents * steps, el
+
+
+def sweep_cpu_baseline(steps=2, scale=1.0):
+    """The 64 sweep simulations on the oracle, one process per host core
+    (spawned: CUDA is already initialised in this process)."""
+    import multiprocessing as mp
+    import workloads as W
+    cores = os.cpu_count() or 1
+    n = len(W.sweep(scale))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_sweep_oracle_task, [(k, steps, scale) for k in range(n)], chunksize=1)
+    ms = sum(r[0] for r in res)
+    busy = sum(r[1] for r in res)
+    return {"value": ms / (busy / cores), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {n} sweep simulations, the first {steps} steps of each from t = 0, serial "
+                      f"oracle in {cores} worker processes; value = molecule-steps / (summed step "
+                      f"seconds / {cores}), creation not timed"}
+
+
+def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0, cpu=True):
     """The 64-sim dose x seed sweep: all sims stepped together in one batch
     versus each sim alone, one after the other (same library, same step count,
     CUDA-graph replay in both, no L2 flush: the batch's 12.6M-agent state
@@ -263,7 +295,8 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0):
         sim.close()
     batched = n_total * steps / (batched_ms / 1e3)
     serial = n_total * steps / (serial_ms / 1e3)
-    return {"sims": len(sims), "agents": n_total, "live_after": live, "steps": steps,
+    cpu_line = sweep_cpu_baseline(scale=scale) if cpu else None
+    return {"cpu_baseline": cpu_line, "sims": len(sims), "agents": n_total, "live_after": live, "steps": steps,
             "autotune": {"cell_delta": best.cell_delta, "blocks_per_sm": best.blocks_per_sm,
                          "candidates": [[c.cell_delta, c.blocks_per_sm, round(c.ms_per_step, 4)] for c in tried]},
             "batched_value": batched, "serial_value": serial, "unit": UNIT,
@@ -327,7 +360,7 @@ def main():
     if args.workload == "sweep":
         stream = torch.cuda.Stream()
         with Clocks(local) as clk:
-            sw = run_sweep(A, torch, stream, args.steps, args.warmup)
+            sw = run_sweep(A, torch, stream, args.steps, args.warmup, cpu=not args.no_cpu_baseline and world == 1)
         line = {"metric": METRIC, "value": sw["batched_value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": sw["batched_ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -445,7 +478,7 @@ def main():
 
     sweep = None
     if args.sweep_steps > 0 and args.workload == "cascade" and not args.agents:
-        sweep = run_sweep(A, torch, stream, args.sweep_steps)
+        sweep = run_sweep(A, torch, stream, args.sweep_steps, cpu=not args.no_cpu_baseline and world == 1)
 
     served = None
     if args.serve_seconds > 0 and args.workload == "cascade" and not args.agents:
