@@ -153,6 +153,12 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def launches_per_step(cells):
+    """Engine kernels one step launches: five, plus k_tile_prefix on grids of
+    more than 8192 scan tiles of 8192 cells."""
+    return 5 + (1 if (cells + 8191) // 8192 > 8192 else 0)
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if the
     kernel sources (kernels.cu + engine.cuh) are unchanged since the capture
@@ -367,7 +373,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "sweep_64_sims_50k_500k", "agents": sw["agents"],
                            "l2": "no flush (batched state 12.6M agents exceeds L2)"},
-                "sweep": sw, "gpu_launches": A.N_STEP_KERNELS * args.steps, "clocks": clk.summary()}
+                "sweep": sw, "gpu_launches": launches_per_step(sw["agents"]) * args.steps, "clocks": clk.summary()}
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
@@ -376,6 +382,7 @@ def main():
     seed = seed + rank                      # independent replicas
     stream = torch.cuda.Stream()
     sim = A.Sim(model, seed, stream=stream)
+    sim_cells = sim.grid_cells()
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     flush_src = None if args.no_flush else torch.ones(64 << 20, dtype=torch.float32, device="cuda")
 
@@ -509,7 +516,7 @@ def main():
             "p50_step_ms": per_step[len(per_step) // 2], "p99_step_ms": per_step[int(0.99 * (len(per_step) - 1))],
             "roofline": roof, "step_roofline": step_roof,
             "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
-            "gpu_launches": A.N_STEP_KERNELS * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
+            "gpu_launches": launches_per_step(sim_cells) * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
             "serve": served, "volume": volume,
             "clocks": clocks, "wall_s_timed_region": wall}
     if rank == 0:
