@@ -48,7 +48,7 @@ typedef enum {
     ABM_EINVAL = -1,     /* invalid model or argument; nothing was created */
     ABM_ENOMEM = -2,     /* device allocation failed or arena too small    */
     ABM_ECUDA = -3,      /* a CUDA runtime call failed                     */
-    ABM_ETIMEOUT = -4,   /* a bounded device-side wait gave up             */
+    ABM_ETIMEOUT = -4,   /* reserved: no call waits on the device today      */
     ABM_ECAPACITY = -5,  /* agents, cells, births or sims exceed capacity  */
     ABM_EDEVICE = -6,    /* no usable CUDA device (sm_103 required)        */
     ABM_ESTATE = -7      /* handle already failed, or bad sim index        */

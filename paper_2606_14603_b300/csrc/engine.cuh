@@ -131,7 +131,7 @@ struct Ctl {
     uint32_t cur;            // current buffer
     uint32_t n_cells;        // cells in use
     uint32_t pad0;
-    uint32_t epoch;          // global step counter (look-back tags)
+    uint32_t epoch;          // global step counter
     uint32_t err;
     uint32_t err_info;
     uint32_t n_sims;         // sim slots in use (upper bound of the table)
