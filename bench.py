@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=20.0,
                    help="seconds of job arrivals in the serving measurement (the served config runs 600)")
     p.add_argument("--sweep-steps", type=int, default=50, help="steps per sim in the sweep summary")
+    p.add_argument("--size-steps", type=int, default=100,
+                   help="steps of the 4M/16M-agent cascade summary (0 = skip)")
     p.add_argument("--volume-steps", type=int, default=4000,
                    help="steps of the volume-invariance summary (1M vs 10M agents per dose; 0 = skip)")
     p.add_argument("--agents", type=int, default=0, help="override the agent count")
@@ -493,6 +495,37 @@ def main():
         served = run_serve(A, args.serve_seconds)
         sim = None
 
+    sizes = None
+    if args.size_steps > 0 and args.workload == "cascade" and not args.agents:
+        if sim is not None:
+            sim.close()
+            sim = None
+        import workloads as W
+        sizes = []
+        for n_big in (4_000_000, 16_000_000):
+            big = W.mapk(n_big)
+            bs = A.Sim(big, W.MAPK_SEED, stream=stream)
+            bs.step(5)
+            bs.sync()
+            t_ms = []
+            for _ in range(args.size_steps):
+                if flush is not None:
+                    flush_l2()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bs.step(1)
+                e1.record(stream)
+                t_ms.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = sorted(a.elapsed_time(b) for a, b in t_ms)
+            live = molecules(bs.counts(), big)
+            rate = live * len(ms) / (sum(ms) / 1e3)
+            sizes.append({"agents": n_big, "steps": len(ms), "value": rate, "unit": UNIT,
+                          "ms_per_step": sum(ms) / len(ms), "p50_step_ms": ms[len(ms) // 2],
+                          "step_roofline_frac": rate * STEP_BYTES_PER_AGENT / 1e9 / hbm,
+                          "l2": "flushed between steps"})
+            bs.close()
+
     volume = None
     if args.volume_steps > 0 and args.workload == "cascade" and not args.agents:
         from paper_2606_14603_b300.experiments import volume_invariance
@@ -517,7 +550,7 @@ def main():
             "roofline": roof, "step_roofline": step_roof,
             "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
             "gpu_launches": launches_per_step(sim_cells) * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
-            "serve": served, "volume": volume,
+            "serve": served, "sizes": sizes, "volume": volume,
             "clocks": clocks, "wall_s_timed_region": wall}
     if rank == 0:
         print(json.dumps(line), flush=True)

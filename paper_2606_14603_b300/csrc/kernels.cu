@@ -755,12 +755,14 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
     for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += nb * blockDim.x) {
         const uint2 e = B.props[k];
         const uint32_t i = e.x, j = e.y;
-        const uint64_t kb = B.acc[j];
-        const uint32_t ida = aid[i];
-        if ((uint32_t)kb != ida || B.acc[i] != kEmpty) continue;
+        // the two meta words are loaded with the slots (one round trip less)
         uint32_t* wa = reinterpret_cast<uint32_t*>(&pm[i]) + 3;
         uint32_t* wb = reinterpret_cast<uint32_t*>(&pm[j]) + 3;
+        const uint64_t kb = B.acc[j];
+        const uint32_t ida = aid[i];
+        const uint64_t ka = B.acc[i];
         uint32_t ma = *wa, mb = *wb;
+        if ((uint32_t)kb != ida || ka != kEmpty) continue;
         const SimDev& S = B.sims[sim_of(ma)];
         const ModelDev& Mo = B.models[S.model];
         const uint32_t r = Mo.rx_of[ma & M_SP][mb & M_SP];
