@@ -267,29 +267,27 @@ def sweep_cpu_baseline(steps=2, scale=1.0):
 
 
 def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0, cpu=True):
-    """The 64-sim dose x seed sweep: all sims stepped together in one batch
-    versus each sim alone, one after the other (same library, same step count,
-    CUDA-graph replay in both, no L2 flush: the batch's 12.6M-agent state
-    exceeds L2 while the small sims alone fit in it)."""
+    """The 64-sim dose x seed sweep: all sims stepped together (one batch, or
+    the autotuner's number of batches on concurrent streams) versus each sim
+    alone, one after the other (same library, same step count, CUDA-graph
+    replay in both, no L2 flush: the batch's 12.6M-agent state exceeds L2
+    while the small sims alone fit in it)."""
     import workloads as W
     from paper_2606_14603_b300 import autotune
     sims = W.sweep(scale)
     models = [m for m, _ in sims]
     n_total = sum(m.n_agents for m in models)
-    best, tried = autotune.tune(sims, cell_deltas=(0, 1), blocks=(0, 16, 32), steps=10, warmup=2)
+    best, tried = autotune.tune(sims, cell_deltas=(0, 1), blocks=(0,), groups=(1, 2, 4, 8), steps=10,
+                                warmup=2)
+    grp = autotune.BatchGroup(sims, best.cell_delta, best.blocks_per_sm, best.groups)
+    grp.step(warmup)
+    grp.sync()
+    torch.cuda.synchronize()
+    batched_ms = grp.timed_step(steps)
+    grp.sync()
+    live = sum(molecules(grp.counts(k), m) for k, m in enumerate(models))
+    grp.close()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    b, ids = autotune.batch_for(sims, best.cell_delta, best.blocks_per_sm, stream=stream)
-    b.step(warmup)
-    b.sync()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    b.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    b.sync()
-    batched_ms = e0.elapsed_time(e1)
-    live = sum(molecules(b.counts(i), m) for i, m in zip(ids, models))
-    b.close()
     serial_ms = 0.0
     for m, s in sims:
         sim = A.Sim(m, s, stream=stream)
@@ -306,7 +304,9 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0, cpu=True):
     cpu_line = sweep_cpu_baseline(scale=scale) if cpu else None
     return {"cpu_baseline": cpu_line, "sims": len(sims), "agents": n_total, "live_after": live, "steps": steps,
             "autotune": {"cell_delta": best.cell_delta, "blocks_per_sm": best.blocks_per_sm,
-                         "candidates": [[c.cell_delta, c.blocks_per_sm, round(c.ms_per_step, 4)] for c in tried]},
+                         "groups": best.groups,
+                         "candidates": [[c.cell_delta, c.blocks_per_sm, c.groups, round(c.ms_per_step, 4)]
+                                        for c in tried]},
             "batched_value": batched, "serial_value": serial, "unit": UNIT,
             "batched_over_serial": batched / serial, "batched_ms_per_step": batched_ms / steps,
             "serial_ms_per_round": serial_ms / steps}

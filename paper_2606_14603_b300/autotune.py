@@ -1,11 +1,15 @@
-"""Autotuner for a batch of simulations: grid cell size and launch shape.
+"""Autotuner for a batch of simulations: grid cell size, launch shape and
+the number of concurrent batches.
 
-Neither knob changes a result (the proposal search covers every partner
-within reach for any cell edge not below the largest contact radius, and the
-kernels are grid-stride loops), so the tuner is free to pick whatever is
-fastest.  It builds trial batches of the given simulations, times a few
-steps of each candidate with CUDA events on the batch's stream, and returns
-the fastest configuration together with all timings.
+No knob changes a result (the proposal search covers every partner within
+reach for any cell edge not below the largest contact radius, the kernels
+are grid-stride loops, and a simulation's arithmetic does not depend on what
+else shares its batch), so the tuner is free to pick whatever is fastest.
+Splitting the simulations over several batches on separate CUDA streams lets
+the latency-bound kernels of one batch overlap the memory-bound kernels of
+another.  The tuner builds trial groups of the given simulations, times a few
+steps of each candidate with CUDA events, and returns the fastest
+configuration together with all timings.
 """
 from __future__ import annotations
 
@@ -21,6 +25,7 @@ class Choice:
     cell_delta: int          # added to each model's automatic cell_log2
     blocks_per_sm: int       # 0 = the CTAs of the move pass that fit on an SM at once
     ms_per_step: float
+    groups: int = 1          # batches stepped concurrently, one CUDA stream each
 
 
 def batch_for(sims: Sequence[Tuple[object, int]], cell_delta: int = 0, blocks_per_sm: int = 0,
@@ -44,22 +49,80 @@ def batch_for(sims: Sequence[Tuple[object, int]], cell_delta: int = 0, blocks_pe
     return b, ids
 
 
-def tune(sims: Sequence[Tuple[object, int]], cell_deltas=(-1, 0, 1), blocks=(0, 8, 16),
+class BatchGroup:
+    """The simulations split over `groups` batches (round-robin by size, so
+    the groups hold similar agent counts), each on its own CUDA stream and
+    stepped together.  Simulation k of the input keeps index k here."""
+
+    def __init__(self, sims: Sequence[Tuple[object, int]], cell_delta: int = 0, blocks_per_sm: int = 0,
+                 groups: int = 1, headroom: float = 1.25, streams=None):
+        import torch
+        groups = max(1, min(groups, len(sims)))
+        order = sorted(range(len(sims)), key=lambda k: sims[k][0].n_agents)
+        members = [order[g::groups] for g in range(groups)]
+        self.streams = streams or [torch.cuda.Stream() for _ in range(groups)]
+        self.batches, self.where = [], {}
+        for g, ks in enumerate(members):
+            b, ids = batch_for([sims[k] for k in ks], cell_delta, blocks_per_sm, headroom, self.streams[g])
+            self.batches.append(b)
+            for k, sid in zip(ks, ids):
+                self.where[k] = (g, sid)
+
+    def step(self, n: int, chunk: int = 8) -> None:
+        """n steps of every batch; launches interleave in chunks so that every
+        stream has work queued."""
+        while n > 0:
+            k = min(n, chunk)
+            for b in self.batches:
+                b.step(k)
+            n -= k
+
+    def sync(self) -> None:
+        for b in self.batches:
+            b.sync()
+
+    def counts(self, k: int):
+        g, sid = self.where[k]
+        return self.batches[g].counts(sid)
+
+    def digest(self, k: int) -> int:
+        g, sid = self.where[k]
+        return self.batches[g].digest(sid)
+
+    def timed_step(self, n: int) -> float:
+        """Milliseconds of n steps of the whole group, from CUDA events joined
+        across the streams (the first stream starts and ends the interval)."""
+        import torch
+        s0 = self.streams[0]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(s0)
+        for st in self.streams[1:]:
+            st.wait_event(start)
+        self.step(n)
+        for st in self.streams[1:]:
+            e = torch.cuda.Event()
+            e.record(st)
+            s0.wait_event(e)
+        end.record(s0)
+        end.synchronize()
+        return start.elapsed_time(end)
+
+    def close(self) -> None:
+        for b in self.batches:
+            b.close()
+        self.batches = []
+
+
+def tune(sims: Sequence[Tuple[object, int]], cell_deltas=(-1, 0, 1), blocks=(0, 8, 16), groups=(1, 2, 4),
          steps: int = 20, warmup: int = 3) -> Tuple[Choice, List[Choice]]:
-    import torch
-    stream = torch.cuda.Stream()
     results = []
-    for d, bps in itertools.product(cell_deltas, blocks):
-        b, _ = batch_for(sims, d, bps, stream=stream)
-        b.step(warmup)
-        b.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.step(steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        b.sync()
-        results.append(Choice(d, bps, e0.elapsed_time(e1) / steps))
-        b.close()
+    for d, bps, ng in itertools.product(cell_deltas, blocks, groups):
+        grp = BatchGroup(sims, d, bps, ng)
+        grp.step(warmup)
+        grp.sync()
+        ms = grp.timed_step(steps)
+        grp.sync()
+        results.append(Choice(d, bps, ms / steps, ng))
+        grp.close()
     best = min(results, key=lambda c: c.ms_per_step)
     return best, results

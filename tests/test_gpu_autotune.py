@@ -1,5 +1,6 @@
 """Autotuner knobs do not change results (GPU): every (cell size, launch
-shape) candidate yields identical digests, equal to the oracle's."""
+shape, concurrent batches) candidate yields identical digests, equal to the
+oracle's."""
 import pytest
 
 import workloads as W
@@ -24,5 +25,11 @@ def test_tuner_candidates_agree_and_match_oracle(oracle_mod):
         b.step(25)
         assert [b.digest(i) for i in ids] == ref, (d, bps)
         b.close()
-    best, allc = autotune.tune(sims, cell_deltas=(0, 1), blocks=(8, 16), steps=5, warmup=1)
-    assert len(allc) == 4 and best.ms_per_step == min(c.ms_per_step for c in allc)
+    for ng in (2, 3):   # simulations split over concurrent batches on their own streams
+        grp = autotune.BatchGroup(sims, 0, 0, ng)
+        grp.step(25)
+        grp.sync()
+        assert [grp.digest(k) for k in range(len(sims))] == ref, ng
+        grp.close()
+    best, allc = autotune.tune(sims, cell_deltas=(0, 1), blocks=(8, 16), groups=(1, 2), steps=5, warmup=1)
+    assert len(allc) == 8 and best.ms_per_step == min(c.ms_per_step for c in allc)
