@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=20.0,
                    help="seconds of job arrivals in the serving measurement (the served config runs 600)")
     p.add_argument("--sweep-steps", type=int, default=50, help="steps per sim in the sweep summary")
+    p.add_argument("--serve-groups", type=int, default=4,
+                   help="batches the server steps concurrently (one CUDA stream each)")
     p.add_argument("--size-steps", type=int, default=100,
                    help="steps of the 4M/16M-agent cascade summary (0 = skip)")
     p.add_argument("--volume-steps", type=int, default=4000,
@@ -312,7 +314,7 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0, cpu=True):
             "serial_ms_per_round": serial_ms / steps}
 
 
-def run_serve(A, seconds, budget=150e9):
+def run_serve(A, seconds, budget=150e9, groups=1):
     """Served workload: Poisson arrivals (20/s, seed 7) of cascade or
     two-compartment jobs, 10k-2M agents, 1k-20k steps, admitted under an HBM
     budget, continuous batching; runs `seconds` of arrivals in real time and
@@ -320,13 +322,14 @@ def run_serve(A, seconds, budget=150e9):
     import workloads as W
     from paper_2606_14603_b300 import serve
     jobs = W.served_jobs(duration_s=seconds)
-    srv = serve.Server(budget_bytes=budget)
+    srv = serve.Server(budget_bytes=budget, groups=groups)
     out = serve.run(jobs, srv, duration_s=seconds, real_time=True, drain=False)
     srv.close()
     out.pop("results")
     out["arrival_rate_per_s"] = 20.0
     out["budget_bytes"] = budget
     out["window_s"] = seconds
+    out["groups"] = groups
     return out
 
 
@@ -354,7 +357,7 @@ def main():
 
     if args.workload == "serve":
         with Clocks(local) as clk:
-            sv = run_serve(A, args.serve_seconds)
+            sv = run_serve(A, args.serve_seconds, groups=args.serve_groups)
         line = {"metric": METRIC, "value": sv["throughput_molecule_steps_per_s"], "unit": UNIT, "n_gpus": world,
                 "steps": sv["steps_run"], "warmup": 0, "ms_per_step": None, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -492,7 +495,7 @@ def main():
     served = None
     if args.serve_seconds > 0 and args.workload == "cascade" and not args.agents:
         sim.close()
-        served = run_serve(A, args.serve_seconds)
+        served = run_serve(A, args.serve_seconds, groups=args.serve_groups)
         sim = None
 
     sizes = None

@@ -18,7 +18,7 @@ from __future__ import annotations
 import dataclasses
 import math
 import time
-from typing import Callable, Dict, List, Optional
+from typing import Callable, Dict, List, Optional, Tuple
 
 import numpy as np
 
@@ -59,29 +59,41 @@ class _Resident:
 class Server:
     """Continuous batching of simulation jobs under an HBM budget.
 
-    budget_bytes: device memory for the shared arena (agents and cells split
-    by `cells_per_agent`, unless capacities are given); max_sims: concurrent
-    jobs; epoch: steps between admission points.  A job is frozen on the
-    device at its own last step, so epochs need not stop at job boundaries."""
+    budget_bytes: device memory for the arenas (agents and cells split by
+    `cells_per_agent`, unless capacities are given); max_sims: concurrent
+    jobs; epoch: steps between admission points; groups: batches stepped
+    concurrently, each on its own CUDA stream with an equal share of the
+    budget and the job slots (the latency-bound kernels of one overlap the
+    memory-bound kernels of another).  A job is frozen on the device at its
+    own last step, so epochs need not stop at job boundaries."""
 
     def __init__(self, budget_bytes: float = 150e9, max_sims: int = 256, epoch: int = 50,
                  cells_per_agent: float = 1.3, headroom: float = 1.25, stream=None,
-                 capacity_agents: Optional[int] = None, capacity_cells: Optional[int] = None):
+                 capacity_agents: Optional[int] = None, capacity_cells: Optional[int] = None,
+                 groups: int = 1):
         per_agent = BYTES_PER_AGENT_SLOT + cells_per_agent * BYTES_PER_CELL
         cap_agents = capacity_agents or min(int(budget_bytes / per_agent), 2_000_000_000)
         cap_cells = capacity_cells or min(int(cap_agents * cells_per_agent), 4_000_000_000)
-        self.cap_agents, self.cap_cells = cap_agents, cap_cells
-        self.max_sims = max_sims
+        self.groups = max(1, groups)
+        # per group
+        self.cap_agents, self.cap_cells = cap_agents // self.groups, cap_cells // self.groups
+        self.max_sims = max(1, max_sims // self.groups)
         self.epoch = epoch
         self.headroom = headroom
-        self.batch = Batch(cap_agents, cap_cells, max_sims, stream=stream)
-        self.resident: Dict[int, _Resident] = {}
-        self.used_agents = 0
-        self.used_cells = 0
+        # one library-owned stream per batch unless a single batch gets the caller's
+        self.batches = [Batch(self.cap_agents, self.cap_cells, self.max_sims,
+                              stream=stream if self.groups == 1 else None) for _ in range(self.groups)]
+        self.resident: Dict[Tuple[int, int], _Resident] = {}
+        self.used_agents = [0] * self.groups
+        self.used_cells = [0] * self.groups
         self.steps_run = 0
         self.molecule_steps = 0
         self.max_resident = 0
         self.waited = 0          # admissions that had to wait for capacity
+
+    @property
+    def batch(self):
+        return self.batches[0]
 
     # -- capacity accounting (reserved per job: initial agents x headroom) --
     def need(self, job):
@@ -91,27 +103,44 @@ class Server:
         a, c = self.need(job)
         return a <= self.cap_agents and c <= self.cap_cells
 
-    def fits(self, job) -> bool:
+    def _group_for(self, job) -> Optional[int]:
         need_a, need_c = self.need(job)
-        return (len(self.resident) < self.max_sims and self.used_agents + need_a <= self.cap_agents
-                and self.used_cells + need_c <= self.cap_cells)
+        best = None
+        for g in range(self.groups):
+            n_res = sum(1 for (gg, _) in self.resident if gg == g)
+            if (n_res < self.max_sims and self.used_agents[g] + need_a <= self.cap_agents
+                    and self.used_cells[g] + need_c <= self.cap_cells):
+                if best is None or self.used_agents[g] < self.used_agents[best]:
+                    best = g
+        return best
+
+    def fits(self, job) -> bool:
+        return self._group_for(job) is not None
 
     def admit(self, job, now: float) -> None:
+        g = self._group_for(job)
         need_a, need_c = self.need(job)
-        sid = self.batch.add(job.model, job.seed)
-        self.batch.set_max_step(sid, job.steps)
-        self.resident[sid] = _Resident(job, sid, job.steps, now, need_a, need_c)
-        self.used_agents += need_a
-        self.used_cells += need_c
+        sid = self.batches[g].add(job.model, job.seed)
+        self.batches[g].set_max_step(sid, job.steps)
+        self.resident[(g, sid)] = _Resident(job, sid, job.steps, now, need_a, need_c)
+        self.used_agents[g] += need_a
+        self.used_cells[g] += need_c
         self.max_resident = max(self.max_resident, len(self.resident))
 
     def step_epoch(self) -> int:
-        """Step the batch for one epoch (at most the largest remaining count);
-        jobs that reach their own last step inside it are frozen there."""
+        """Step every batch with resident jobs for one epoch (at most the
+        largest remaining count); jobs that reach their own last step inside
+        it are frozen there.  Launches interleave across the batches."""
         if not self.resident:
             return 0
         k = min(max(r.remaining for r in self.resident.values()), self.epoch)
-        self.batch.step(k)
+        active = sorted({g for (g, _) in self.resident})
+        left = k
+        while left > 0:
+            c = min(left, 8)
+            for g in active:
+                self.batches[g].step(c)
+            left -= c
         for r in self.resident.values():
             done = min(k, r.remaining)
             r.remaining -= done
@@ -121,20 +150,26 @@ class Server:
 
     def retire_finished(self, clock: Callable[[], float]) -> List[JobResult]:
         done = []
-        for sid in [s for s, r in self.resident.items() if r.remaining == 0]:
-            r = self.resident.pop(sid)
-            counts = self.batch.counts(sid)
-            digest = self.batch.digest(sid)
+        for key in [key for key, r in self.resident.items() if r.remaining == 0]:
+            g, sid = key
+            r = self.resident.pop(key)
+            counts = self.batches[g].counts(sid)
+            digest = self.batches[g].digest(sid)
             now = clock()
-            self.batch.remove(sid)
-            self.used_agents -= r.agents
-            self.used_cells -= r.cells
+            self.batches[g].remove(sid)
+            self.used_agents[g] -= r.agents
+            self.used_cells[g] -= r.cells
             done.append(JobResult(r.job.job_id, r.job.arrival_s, r.admitted_s, now, r.job.steps,
                                   r.job.model.n_agents, counts, digest))
         return done
 
+    def sync(self) -> None:
+        for b in self.batches:
+            b.sync()
+
     def close(self) -> None:
-        self.batch.close()
+        for b in self.batches:
+            b.close()
 
 
 def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: bool = True,
@@ -177,7 +212,7 @@ def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: boo
             w0 = time.perf_counter()
             server.step_epoch()
             if not real_time:
-                server.batch.sync()     # the virtual clock advances by GPU time
+                server.sync()           # the virtual clock advances by GPU time
             results += server.retire_finished(clock)
             if not real_time:
                 virtual[0] += time.perf_counter() - w0

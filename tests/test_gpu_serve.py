@@ -25,14 +25,17 @@ def _jobs():
     return [W.Job(k, t, m, s, n) for k, (t, m, s, n) in enumerate(specs)]
 
 
-def test_served_jobs_equal_alone_runs():
+@pytest.mark.parametrize("groups", [1, 2])
+def test_served_jobs_equal_alone_runs(groups):
     require_gpu()
     A = engine()
     from paper_2606_14603_b300 import serve
     jobs = _jobs()
     # small capacities: not all jobs fit at once, so admission has to wait
     caps = [A.model_grid(j.model)[1] for j in jobs]
-    srv = serve.Server(capacity_agents=45_000, capacity_cells=2 * max(caps), max_sims=3, epoch=25)
+    # one batch: 45k agent slots and 3 jobs; two batches: one job slot each
+    srv = serve.Server(capacity_agents=45_000 * groups, capacity_cells=2 * max(caps) * groups,
+                       max_sims=3 if groups == 1 else groups, epoch=25, groups=groups)
     out = serve.run(jobs, srv, real_time=False)
     srv.close()
     assert out["jobs_completed"] == len(jobs) and out["jobs_rejected"] == 0
