@@ -326,6 +326,7 @@ def run_serve(A, seconds, budget=150e9, groups=1):
     out = serve.run(jobs, srv, duration_s=seconds, real_time=True, drain=False)
     srv.close()
     out.pop("results")
+    out.pop("failed")
     out["arrival_rate_per_s"] = 20.0
     out["budget_bytes"] = budget
     out["window_s"] = seconds

@@ -314,6 +314,13 @@ void        abm_ncdf_table(int16_t* out65536);
  * host arrays ctr[4n], key[2n]; writes out[4n] (host).  Synchronous. */
 abm_status  abm_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                              size_t n);
+/* Testing hook (host-side failure injection; no counterpart in the paper):
+ * the next abm_step / abm_batch_step call in this process reports
+ * `cuda_error` (a cudaError_t value, nonzero) as the result of its launch
+ * without launching anything, so the call returns ABM_ECUDA and the handle
+ * becomes destroy-only (ABM_ESTATE), exactly as after a real launch failure.
+ * The device and other handles are unaffected.  0 clears a pending injection. */
+void        abm_debug_inject_launch_error(int cuda_error);
 /* Library version string. */
 const char* abm_version(void);
 

@@ -142,6 +142,7 @@ def lib():
             "abm_kernel_name": (C.c_char_p, [C.c_uint32]),
             "abm_grid_cells": (C.c_int, [P, C.POINTER(C.c_uint64)]),
             "abm_model_grid": (C.c_int, [C.POINTER(Model), C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
+            "abm_debug_inject_launch_error": (None, [C.c_int]),
             "abm_monitor_set": (C.c_int, [P, C.POINTER(Monitor), P, C.c_size_t]),
             "abm_monitor_clear": (C.c_int, [P]),
             "abm_monitor_read": (C.c_int, [P, C.POINTER(MonitorStateC), P, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -493,6 +494,12 @@ def ncdf_table() -> np.ndarray:
     out = np.zeros(65536, dtype=np.int16)
     lib().abm_ncdf_table(out.ctypes.data)
     return out
+
+
+def inject_launch_error(cuda_error: int) -> None:
+    """Testing hook: the next step call fails as if its launch had returned
+    this CUDA error (host side only; see include/abm.h)."""
+    lib().abm_debug_inject_launch_error(cuda_error)
 
 
 def device_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:

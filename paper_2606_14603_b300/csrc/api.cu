@@ -10,6 +10,7 @@
 //   thresholds  floor(p * 2^32)
 //   radius      llround(radius_nm / unit_nm)
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -318,6 +319,10 @@ abm_status fail(abm_batch* b, abm_status st, const std::string& msg) {
 abm_status cuda_fail(abm_batch* b, cudaError_t e, const char* where) {
     return fail(b, ABM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+// Host-side failure injection for tests: the next step call reports this
+// CUDA error as the result of its launch, without launching anything.
+std::atomic<int> g_inject_launch_error{0};
 
 #define CU(call)                                              \
     do {                                                      \
@@ -941,6 +946,8 @@ abm_status abm_batch_set_max_step(abm_batch* b, int32_t sim, uint32_t max_step) 
 abm_status abm_batch_step(abm_batch* b, uint32_t n) {
     if (!b) return ABM_EINVAL;
     if (b->failed) return ABM_ESTATE;
+    if (const int inj = g_inject_launch_error.exchange(0))
+        return cuda_fail(b, (cudaError_t)inj, "cudaGraphLaunch (injected)");
     if (n > 0)
         for (auto& h : b->sims)
             if (h.state == 2) h.state = 0;  // their agents are dropped by this step
@@ -1245,6 +1252,8 @@ void abm_destroy(abm_sim* s) {
     abm_batch_destroy(s->b);
     delete s;
 }
+
+void abm_debug_inject_launch_error(int cuda_error) { g_inject_launch_error.store(cuda_error); }
 
 abm_status abm_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n) {
     if (!ctr || !key || !out) return ABM_EINVAL;

@@ -9,6 +9,9 @@ its arrival to the moment its result is back on the host.
 
 The engine's arithmetic does not depend on what else is in the batch, so every
 job's result is bit-identical to the same job run alone (tests check this).
+A device error in a batch (e.g. a job whose births exceed the per-step limit)
+fails the jobs resident in that batch, which are reported with the error;
+the batch is replaced and serving goes on.
 
 This is host-side orchestration over the C ABI: admission, retirement and
 epoch sizing happen here, every step runs in the engine's kernels.
@@ -22,7 +25,7 @@ from typing import Callable, Dict, List, Optional, Tuple
 
 import numpy as np
 
-from . import Batch, model_grid
+from . import AbmError, Batch, model_grid
 
 # bytes of one agent slot and one grid cell in the batch arena (see the
 # layout in csrc/api.cu); used only to turn an HBM budget into capacities
@@ -38,8 +41,9 @@ class JobResult:
     finished_s: float
     steps: int
     agents: int
-    counts: np.ndarray
-    digest: int
+    counts: Optional[np.ndarray]
+    digest: Optional[int]
+    error: Optional[str] = None
 
     @property
     def latency_s(self) -> float:
@@ -86,10 +90,13 @@ class Server:
         self.resident: Dict[Tuple[int, int], _Resident] = {}
         self.used_agents = [0] * self.groups
         self.used_cells = [0] * self.groups
+        self.stream = stream
         self.steps_run = 0
         self.molecule_steps = 0
         self.max_resident = 0
         self.waited = 0          # admissions that had to wait for capacity
+        self.failed: List[JobResult] = []   # jobs lost to a batch failure, not yet reported
+        self.batch_failures = 0
 
     @property
     def batch(self):
@@ -117,10 +124,31 @@ class Server:
     def fits(self, job) -> bool:
         return self._group_for(job) is not None
 
+    def _fail_group(self, g: int, err: str, now: float) -> None:
+        """Batch g reported a device error: its resident jobs fail; a fresh
+        batch takes its place."""
+        for key in [k for k in self.resident if k[0] == g]:
+            r = self.resident.pop(key)
+            self.failed.append(JobResult(r.job.job_id, r.job.arrival_s, r.admitted_s, now, r.job.steps,
+                                         r.job.model.n_agents, None, None, err))
+        self.used_agents[g] = 0
+        self.used_cells[g] = 0
+        self.batches[g].close()
+        self.batches[g] = Batch(self.cap_agents, self.cap_cells, self.max_sims,
+                                stream=self.stream if self.groups == 1 else None)
+        self.batch_failures += 1
+
     def admit(self, job, now: float) -> None:
         g = self._group_for(job)
         need_a, need_c = self.need(job)
-        sid = self.batches[g].add(job.model, job.seed)
+        try:
+            sid = self.batches[g].add(job.model, job.seed)
+        except AbmError as e:
+            if e.status in (-1, -5):   # EINVAL / ECAPACITY of this job: the batch is intact
+                raise
+            self._fail_group(g, str(e), now)   # an earlier device error surfaced here
+            g = self._group_for(job)
+            sid = self.batches[g].add(job.model, job.seed)
         self.batches[g].set_max_step(sid, job.steps)
         self.resident[(g, sid)] = _Resident(job, sid, job.steps, now, need_a, need_c)
         self.used_agents[g] += need_a
@@ -139,7 +167,10 @@ class Server:
         while left > 0:
             c = min(left, 8)
             for g in active:
-                self.batches[g].step(c)
+                try:
+                    self.batches[g].step(c)
+                except AbmError:
+                    pass        # reported by the next synchronising call of this batch
             left -= c
         for r in self.resident.values():
             done = min(k, r.remaining)
@@ -149,7 +180,12 @@ class Server:
         return k
 
     def retire_finished(self, clock: Callable[[], float]) -> List[JobResult]:
-        done = []
+        for g in sorted({g for (g, _) in self.resident}):
+            try:
+                self.batches[g].sync()
+            except AbmError as e:
+                self._fail_group(g, str(e), clock())
+        done, self.failed = self.failed, []
         for key in [key for key, r in self.resident.items() if r.remaining == 0]:
             g, sid = key
             r = self.resident.pop(key)
@@ -165,7 +201,10 @@ class Server:
 
     def sync(self) -> None:
         for b in self.batches:
-            b.sync()
+            try:
+                b.sync()
+            except AbmError:
+                pass            # handled by retire_finished
 
     def close(self) -> None:
         for b in self.batches:
@@ -227,6 +266,8 @@ def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: boo
         if not drain and clock() >= horizon:
             break
     wall = clock()
+    failed = [r for r in results if r.error is not None]
+    results = [r for r in results if r.error is None]
     lat = np.array([r.latency_s for r in results]) if results else np.zeros(0)
     offered = sum(j.model.n_agents * j.steps for j in pending if j.arrival_s < horizon)
     return {
@@ -241,8 +282,11 @@ def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: boo
         "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
         "latency_max_s": float(lat.max()) if len(lat) else None,
         "jobs_rejected": len(rejected),
+        "jobs_failed": len(failed),
+        "batch_failures": server.batch_failures,
         "steps_run": server.steps_run,
         "max_resident": server.max_resident,
         "admissions_waited": server.waited,
         "results": results,
+        "failed": failed,
     }

@@ -34,7 +34,7 @@ def _curand_lib():
 
 def test_philox_engine_oracle_curand_device(A, oracle_mod):
     rng = np.random.default_rng(1234)
-    n = 1 << 16
+    n = 1 << 20
     ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
     key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
     ctr[:16] = [[i, 0, 0, 0] for i in range(16)]           # small counters too
@@ -196,6 +196,43 @@ def test_torch_arena_and_stream(A, oracle_mod):
     o.step(30)
     assert g.digest() == o.digest()
     g.close()
+
+
+def test_arena_too_small_or_misaligned_is_refused(A):
+    import torch
+    m = W.toy()
+    nbytes = A.arena_bytes(m)
+    small = torch.empty(nbytes - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(A.AbmError) as e:
+        A.Sim(m, 1, arena=small)
+    assert e.value.status == A.ENOMEM
+    big = torch.empty(nbytes + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(A.AbmError) as e:
+        A.Sim(m, 1, arena=big[16:])                         # not 256-byte aligned
+    assert e.value.status == A.ENOMEM
+
+
+def test_injected_launch_failure_leaves_a_destroyable_handle(A, oracle_mod):
+    """Host-side failure injection: a step whose launch 'fails' returns ECUDA,
+    the handle refuses further work (ESTATE) but is destroyed cleanly, and the
+    device keeps working for other handles."""
+    m = W.toy()
+    g = A.Sim(m, 1)
+    g.step(3)
+    A.inject_launch_error(701)          # cudaErrorLaunchOutOfResources, reported, not raised on the device
+    with pytest.raises(A.AbmError) as e:
+        g.step(1)
+    assert e.value.status == A.ECUDA and "injected" in str(e.value)
+    with pytest.raises(A.AbmError) as e:
+        g.counts()
+    assert e.value.status == A.ESTATE
+    g.close()
+    h = A.Sim(m, 1)
+    h.step(10)
+    o = oracle_mod.OracleSim(m, 1)
+    o.step(10)
+    assert h.digest() == o.digest()
+    h.close()
 
 
 def test_edge_cases(A, oracle_mod):

@@ -62,3 +62,31 @@ def test_server_rejects_jobs_that_can_never_fit():
     out = serve.run(jobs, srv, real_time=False)
     srv.close()
     assert out["jobs_rejected"] == 1 and out["jobs_completed"] == 1
+
+
+def test_a_failing_batch_fails_only_its_jobs():
+    """A job whose births exceed the per-step limit makes its batch report
+    ECAPACITY: the jobs resident in that batch are reported failed, the batch
+    is replaced, and the other batch's jobs (and later jobs) complete, equal
+    to their alone runs."""
+    require_gpu()
+    A = engine()
+    from paper_2606_14603_b300 import serve
+    flood = W.Model("flood", [W.Species("G", 20_000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
+                    [W.Compartment(W.CUBE, 2.0)])
+    jobs = [W.Job(0, 0.000, W.mapk(12_000), 3, 80),
+            W.Job(1, 0.001, flood, 4, 30),
+            W.Job(2, 0.050, W.mapk(9_000, drug_frac=0.0), 5, 60)]
+    caps = [A.model_grid(j.model)[1] for j in jobs]
+    srv = serve.Server(capacity_agents=2 * 40_000, capacity_cells=4 * max(caps), max_sims=2, epoch=20, groups=2)
+    out = serve.run(jobs, srv, real_time=False)
+    srv.close()
+    assert out["jobs_failed"] == 1 and out["batch_failures"] == 1
+    assert [r.job_id for r in out["failed"]] == [1] and "births" in out["failed"][0].error
+    assert sorted(r.job_id for r in out["results"]) == [0, 2]
+    for r in out["results"]:
+        j = jobs[r.job_id]
+        alone = A.Sim(j.model, j.seed)
+        alone.step(j.steps)
+        assert r.digest == alone.digest(), f"job {j.job_id}"
+        alone.close()
