@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -54,6 +55,17 @@ void build_table(int16_t* out) {
         out[i] = (int16_t)-mag;
         out[65535 - i] = mag;
     }
+}
+
+// The default table, built once per process (about 13 ms of host work).
+const int16_t* default_table() {
+    static std::vector<int16_t> table;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        table.resize(65536);
+        build_table(table.data());
+    });
+    return table.data();
 }
 
 uint64_t threshold(double p) { return (uint64_t)std::floor(p * 4294967296.0); }
@@ -280,6 +292,8 @@ struct abm_batch {
     Buffers B{};
     Launch L{};
     uint32_t* staging = nullptr;
+    Ctl* h_ctl = nullptr;                // pinned host copies: control block ...
+    uint64_t* h_counts = nullptr;        // ... and one simulation's counts (512 words)
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;
     struct HostSim {
         int state = 0;  // 0 free, 1 active, 2 draining (removed, not yet stepped)
@@ -356,9 +370,9 @@ abm_status check_device(std::string* msg) {
 // Map the sticky device error word to a status.
 abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
     if (b->failed) return ABM_ESTATE;
-    Ctl h;
-    CU(cudaMemcpyAsync(&h, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaMemcpyAsync(b->h_ctl, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     CU(cudaStreamSynchronize(b->stream));
+    const Ctl h = *b->h_ctl;
     if (out_ctl) *out_ctl = h;
     if (h.err == ERR_NONE) return ABM_OK;
     char buf[160];
@@ -456,7 +470,7 @@ extern "C" {
 const char* abm_version(void) { return "abm-b300 1.0 (sm_103a)"; }
 
 void abm_ncdf_table(int16_t* out) {
-    if (out) build_table(out);
+    if (out) std::memcpy(out, default_table(), 2 * 65536);
 }
 
 size_t abm_batch_arena_bytes(const abm_batch_options* o) {
@@ -507,6 +521,11 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     } else {
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return destroy_and(ABM_ECUDA);
         b->own_stream = true;
+    }
+    if (cudaMallocHost((void**)&b->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_counts, 8 * 512) != cudaSuccess) {
+        cudaGetLastError();
+        return destroy_and(ABM_ENOMEM);
     }
     char* a = b->arena;
     int k = 0;
@@ -573,8 +592,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     b->L.prefix_kernel = B.n_tiles_max > kDirectTiles;
 
     std::vector<int16_t> table(65536);
-    if (o->ncdf_table) std::memcpy(table.data(), o->ncdf_table, 2 * 65536);
-    else build_table(table.data());
+    std::memcpy(table.data(), o->ncdf_table ? o->ncdf_table : default_table(), 2 * 65536);
 #undef CU
 #define CU(call)                                                      \
     do {                                                              \
@@ -1012,9 +1030,12 @@ abm_status abm_batch_counts(abm_batch* b, int32_t sim, uint64_t* out, size_t cap
     if (st != ABM_OK) return st;
     const size_t n = b->sims[sim].n_counts;
     if (n_out) *n_out = n;
-    if (out && cap) CU(cudaMemcpyAsync(out, b->B.counts + (size_t)sim * 512, 8 * std::min(cap, n),
+    // through the pinned staging copy: the copy stays asynchronous, and one
+    // synchronisation covers it and the error check
+    if (out && cap) CU(cudaMemcpyAsync(b->h_counts, b->B.counts + (size_t)sim * 512, 8 * std::min(cap, n),
                                        cudaMemcpyDeviceToHost, b->stream));
     st = sync_and_check(b);
+    if (st == ABM_OK && out && cap) std::memcpy(out, b->h_counts, 8 * std::min(cap, n));
     if (st == ABM_OK && out && cap < n) return ABM_EINVAL;
     return st;
 }
@@ -1023,8 +1044,10 @@ abm_status abm_batch_digest(abm_batch* b, int32_t sim, uint64_t* out) {
     if (!b || !out) return ABM_EINVAL;
     abm_status st = observe(b, sim, 1);
     if (st != ABM_OK) return st;
-    CU(cudaMemcpyAsync(out, b->B.digests + sim, 8, cudaMemcpyDeviceToHost, b->stream));
-    return sync_and_check(b);
+    CU(cudaMemcpyAsync(b->h_counts, b->B.digests + sim, 8, cudaMemcpyDeviceToHost, b->stream));
+    st = sync_and_check(b);
+    if (st == ABM_OK) *out = b->h_counts[0];
+    return st;
 }
 
 abm_status abm_batch_dump(abm_batch* b, int32_t sim, abm_record* out, size_t cap, size_t* n_out) {
@@ -1083,6 +1106,8 @@ void abm_batch_destroy(abm_batch* b) {
     if (b->g8) cudaGraphExecDestroy(b->g8);
     if (b->own_arena && b->arena) cudaFree(b->arena);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    if (b->h_counts) cudaFreeHost(b->h_counts);
     delete b;
 }
 
