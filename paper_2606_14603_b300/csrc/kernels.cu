@@ -1,9 +1,10 @@
 // kernels.cu — the per-step CUDA kernels (sm_103a) of the molecule-agent engine.
 //
 // One step (paper Sec. 2: diffusion, proximity binding, product release,
-// expression, degradation, compartment migration) is six launches over the
-// whole batch of simulations, all reading their sizes from the device
-// control block so that a captured CUDA graph replays them unchanged:
+// expression, degradation, compartment migration) is five launches over the
+// whole batch of simulations (six on grids of more than 8192 scan tiles),
+// all reading their sizes from the device control block so that a captured
+// CUDA graph replays them unchanged:
 //
 //   k_move      P1 events + P2 Brownian move + cell key + histogram rank
 //               (and agents per tile of 8192 cells)
