@@ -587,7 +587,10 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.propose_chunk = (uint32_t)chunk;
     b->L.blocks_propose =
         (int)std::max<uint64_t>(1, std::min<uint64_t>((b->cap_agents + chunk - 1) / chunk, (uint64_t)sms * 32));
-    b->L.blocks_scan = (int)std::max<uint64_t>(1, std::min<uint64_t>(B.n_tiles_max, (uint64_t)sms * 4));
+    // one scan tile per CTA up to 2048 tiles (the hardware overlaps the tiles'
+    // load-scan-store chains; each CTA adds up at most 2048 tile counts before
+    // its own), contiguous tile ranges per CTA beyond
+    b->L.blocks_scan = (int)std::max<uint64_t>(1, std::min<uint64_t>(B.n_tiles_max, 2048));
     b->L.blocks_accept = sms;
     b->L.prefix_kernel = B.n_tiles_max > kDirectTiles;
 
