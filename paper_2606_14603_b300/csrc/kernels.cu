@@ -421,9 +421,14 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(Buffers B) {
     pdl_trigger();
 }
 
-// One scan tile: start[c] = prefix (agents in the tiles before) + the tile's
-// own exclusive prefix; its counts are reset to zero for the next step.
-__device__ __forceinline__ void scan_tile(Buffers& B, uint32_t tile, uint32_t prefix, uint32_t* s_warp) {
+// One scan tile: start[c] = agents in the tiles before + the tile's own
+// exclusive prefix; its counts are reset to zero for the next step.  The
+// agents before the tile are `prefix` plus, when pre_n > 0, the counts of
+// tiles [pre_first, pre_first + pre_n) added up here after this tile's own
+// counts have been requested, so that both sets of loads are in flight at
+// once.  Returns the agents before the next tile.
+__device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_t prefix, uint32_t pre_first,
+                                              uint32_t pre_n, uint32_t* s_warp) {
     const uint32_t base = tile * kScanTile + threadIdx.x * kScanV;
     uint32_t v[kScanV];
     uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
@@ -434,11 +439,20 @@ __device__ __forceinline__ void scan_tile(Buffers& B, uint32_t tile, uint32_t pr
         v[4 * k + 1] = u.y;
         v[4 * k + 2] = u.z;
         v[4 * k + 3] = u.w;
-        src[k] = make_uint4(0, 0, 0, 0);
     }
+    uint32_t pre_v = 0;
+    for (uint32_t t = pre_first + threadIdx.x; t < pre_first + pre_n; t += blockDim.x)
+        pre_v += B.tcnt[t * kTileStride];
+#pragma unroll
+    for (int k = 0; k < kScanV / 4; k++) src[k] = make_uint4(0, 0, 0, 0);
     uint32_t tsum = 0;
 #pragma unroll
     for (int k = 0; k < kScanV; k++) tsum += v[k];
+    if (pre_n) {
+        uint32_t pre_total;
+        block_exclusive_scan(pre_v, s_warp, &pre_total);
+        prefix += pre_total;
+    }
     uint32_t total;
     uint32_t run = prefix + block_exclusive_scan(tsum, s_warp, &total);
     uint4* dst = reinterpret_cast<uint4*>(B.start + base);
@@ -451,6 +465,7 @@ __device__ __forceinline__ void scan_tile(Buffers& B, uint32_t tile, uint32_t pr
         o.w = run; run += v[4 * k + 3];
         dst[k] = o;
     }
+    return prefix + total;
 }
 
 // k_scan: block b scans a contiguous range of tiles; the agents before the
@@ -466,21 +481,10 @@ __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
     const uint32_t t0 = min(ntiles, blockIdx.x * per), t1 = min(ntiles, t0 + per);
     if (t0 < t1) {
-        uint32_t before;
-        if (ntiles <= kDirectTiles) {
-            uint32_t v = 0;
-            for (uint32_t t = threadIdx.x; t < t0; t += blockDim.x) v += B.tcnt[t * kTileStride];
-            uint32_t total;
-            block_exclusive_scan(v, s_warp, &total);
-            before = total;
-        } else {
-            before = B.tsum[t0];
-        }
-        for (uint32_t t = t0; t < t1; t++) {
-            const uint32_t own = B.tcnt[t * kTileStride];
-            scan_tile(B, t, before, s_warp);
-            before += own;
-        }
+        const bool direct = ntiles <= kDirectTiles;
+        uint32_t before = direct ? 0u : B.tsum[t0];
+        for (uint32_t t = t0; t < t1; t++)
+            before = scan_tile(B, t, before, 0, (direct && t == t0) ? t0 : 0, s_warp);
         if (t1 == ntiles && threadIdx.x == 0) {
             B.start[n] = before;  // cells past n are empty
             ctl->n_sorted = before;
