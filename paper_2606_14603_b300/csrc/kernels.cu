@@ -613,21 +613,31 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
     const int4* __restrict__ pm = B.pm[nxt];
     const uint32_t* __restrict__ aid = B.aid[nxt];
     const uint32_t* __restrict__ start = B.start;
-    const int lane = threadIdx.x & 31;
     const uint32_t chunk = B.propose_chunk;
-    if (threadIdx.x == 0) *s_n = 0;
-    __syncthreads();
-    for (uint32_t u = 0; u < chunk / kThreads; u++) {
-        const uint32_t i = base + u * kThreads + threadIdx.x;
-        const bool isp = i < n && B.pflag[i];
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, isp);
-        uint32_t pos = 0;
-        if (lane == 0 && bal) pos = atomicAdd(s_n, (uint32_t)__popc(bal));
-        pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
-        if (isp) s_list[pos + __popc(bal & ((1u << lane) - 1u))] = i;
+    // each thread takes chunk / 256 consecutive flags (4, 8 or 16 bytes, read
+    // as whole words, all requested at once) and places its proposers after
+    // those of the threads before it (order within the list is free)
+    const uint32_t per = chunk / kThreads, i0 = base + threadIdx.x * per;
+    const uint32_t* fw = reinterpret_cast<const uint32_t*>(B.pflag + i0);  // i0 % 4 == 0
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if ((uint32_t)k < per / 4 && i0 + 4 * k < n) w[k] = fw[k];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {  // flags past n are not agents of this step
+        const uint32_t first = i0 + 4 * k;
+        if (first < n && n - first < 4) w[k] &= (1u << (8 * (n - first))) - 1u;
     }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) mine += __popc(w[k]);  // flags are 0 or 1 bytes
+    uint32_t total;
+    uint32_t pos = block_exclusive_scan(mine, reinterpret_cast<uint32_t*>(s_n) + 1, &total);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        for (uint32_t x = w[k]; x; x &= x - 1) s_list[pos++] = i0 + 4 * k + (__ffs(x) - 1) / 8;
     __syncthreads();
-    const uint32_t np = *s_n;
+    const uint32_t np = total;
     for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
         const uint32_t gi = s_list[k];
         const int4 p = pm[gi];
@@ -658,13 +668,13 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
 
 __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     extern __shared__ uint32_t s_list[];  // B.propose_chunk entries
-    __shared__ uint32_t s_n;
+    __shared__ uint32_t s_n[1 + kThreads / 32];  // scratch of the compaction's block scan
     pdl_wait();
     if (ld_volatile(&B.ctl->err)) return;
     const uint32_t n = B.ctl->n_sorted;
     const uint32_t chunk = B.propose_chunk;
     for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk)
-        propose_chunk(B, base, n, s_list, &s_n);
+        propose_chunk(B, base, n, s_list, s_n);
     pdl_trigger();
 }
 
