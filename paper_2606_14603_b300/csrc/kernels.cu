@@ -638,9 +638,16 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         for (uint32_t x = w[k]; x; x &= x - 1) s_list[pos++] = i0 + 4 * k + (__ffs(x) - 1) / 8;
     __syncthreads();
     const uint32_t np = total;
+    // the next proposer's record is requested while this one searches
+    uint32_t gi_n = threadIdx.x < np ? s_list[threadIdx.x] : 0u;
+    int4 p_n = threadIdx.x < np ? pm[gi_n] : make_int4(0, 0, 0, 0);
     for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
-        const uint32_t gi = s_list[k];
-        const int4 p = pm[gi];
+        const uint32_t gi = gi_n;
+        const int4 p = p_n;
+        if (k + blockDim.x < np) {
+            gi_n = s_list[k + blockDim.x];
+            p_n = pm[gi_n];
+        }
         const uint32_t meta = (uint32_t)p.w;
         const SimDev& S = B.sims[sim_of(meta)];
         if (S.step >= S.max_step) continue;  // frozen simulation
@@ -652,15 +659,23 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         const int xlo = max((p.x - rmax) >> sh, 0), xhi = min((p.x + rmax) >> sh, g - 1);
         const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
         const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
+        // the box meets at most 2 cells per axis (a cell is never smaller than a
+        // contact radius): up to 4 x-rows; all their bounds are requested at once
+        uint32_t ra[4], rb[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int zz = zlo + (r >> 1), yy = ylo + (r & 1);
+            const bool in = zz <= zhi && yy <= yhi;
+            const uint32_t row = S.cell_off + ((uint32_t)min(zz, zhi) * g + (uint32_t)min(yy, yhi)) * g;
+            ra[r] = in ? start[row + xlo] : 0u;
+            rb[r] = in ? start[row + xhi + 1] : 0u;
+        }
         Best best;
         uint32_t ida = kNone;
-        for (int zz = zlo; zz <= zhi; zz++)
-            for (int yy = ylo; yy <= yhi; yy++) {
-                const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
-                const uint32_t j1 = start[row + xhi + 1];
-                for (uint32_t j = start[row + xlo]; j < j1; j++)
-                    if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
-            }
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            for (uint32_t j = ra[r]; j < rb[r]; j++)
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
         claim(B, best, ida, gi);
     }
     __syncthreads();  // s_list and s_n are reused by the next chunk
