@@ -674,8 +674,13 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         uint32_t ida = kNone;
 #pragma unroll
         for (int r = 0; r < 4; r++)
-            for (uint32_t j = ra[r]; j < rb[r]; j++)
-                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
+            for (uint32_t j = ra[r]; j < rb[r]; j += 2) {  // two candidate records in flight
+                const bool two = j + 1 < rb[r];
+                const int4 q0 = pm[j];
+                const int4 q1 = two ? pm[j + 1] : q0;
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q0, j, aid, S.step, best);
+                if (two && j + 1 != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q1, j + 1, aid, S.step, best);
+            }
         claim(B, best, ida, gi);
     }
     __syncthreads();  // s_list and s_n are reused by the next chunk
