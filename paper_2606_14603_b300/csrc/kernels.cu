@@ -659,28 +659,42 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         const int xlo = max((p.x - rmax) >> sh, 0), xhi = min((p.x + rmax) >> sh, g - 1);
         const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
         const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
-        // the box meets at most 2 cells per axis (a cell is never smaller than a
-        // contact radius): up to 4 x-rows; all their bounds are requested at once
-        uint32_t ra[4], rb[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const int zz = zlo + (r >> 1), yy = ylo + (r & 1);
-            const bool in = zz <= zhi && yy <= yhi;
-            const uint32_t row = S.cell_off + ((uint32_t)min(zz, zhi) * g + (uint32_t)min(yy, yhi)) * g;
-            ra[r] = in ? start[row + xlo] : 0u;
-            rb[r] = in ? start[row + xhi + 1] : 0u;
-        }
         Best best;
         uint32_t ida = kNone;
-#pragma unroll
-        for (int r = 0; r < 4; r++)
-            for (uint32_t j = ra[r]; j < rb[r]; j += 2) {  // two candidate records in flight
-                const bool two = j + 1 < rb[r];
+        // x-consecutive cells of one (z, y) row form one contiguous range of
+        // the sorted array; walked two candidate records at a time
+        auto walk = [&](uint32_t a, uint32_t b) {
+            for (uint32_t j = a; j < b; j += 2) {
+                const bool two = j + 1 < b;
                 const int4 q0 = pm[j];
                 const int4 q1 = two ? pm[j + 1] : q0;
                 if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q0, j, aid, S.step, best);
                 if (two && j + 1 != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q1, j + 1, aid, S.step, best);
             }
+        };
+        if (zhi - zlo <= 1 && yhi - ylo <= 1) {
+            // the usual box (2 * rmax below the cell edge): at most 2 x 2 rows,
+            // whose bounds are all requested at once
+            uint32_t ra[4], rb[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int zz = zlo + (r >> 1), yy = ylo + (r & 1);
+                const bool in = zz <= zhi && yy <= yhi;
+                const uint32_t row = S.cell_off + ((uint32_t)min(zz, zhi) * g + (uint32_t)min(yy, yhi)) * g;
+                ra[r] = in ? start[row + xlo] : 0u;
+                rb[r] = in ? start[row + xhi + 1] : 0u;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r++) walk(ra[r], rb[r]);
+        } else {
+            // a box wider than half a cell can meet 3 cells per axis (a cell is
+            // never smaller than a contact radius): up to 3 x 3 rows
+            for (int zz = zlo; zz <= zhi; zz++)
+                for (int yy = ylo; yy <= yhi; yy++) {
+                    const uint32_t row = S.cell_off + ((uint32_t)zz * g + (uint32_t)yy) * g;
+                    walk(start[row + xlo], start[row + xhi + 1]);
+                }
+        }
         claim(B, best, ida, gi);
     }
     __syncthreads();  // s_list and s_n are reused by the next chunk
