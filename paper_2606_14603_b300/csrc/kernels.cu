@@ -664,13 +664,8 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         // x-consecutive cells of one (z, y) row form one contiguous range of
         // the sorted array; walked two candidate records at a time
         auto walk = [&](uint32_t a, uint32_t b) {
-            for (uint32_t j = a; j < b; j += 2) {
-                const bool two = j + 1 < b;
-                const int4 q0 = pm[j];
-                const int4 q1 = two ? pm[j + 1] : q0;
-                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q0, j, aid, S.step, best);
-                if (two && j + 1 != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q1, j + 1, aid, S.step, best);
-            }
+            for (uint32_t j = a; j < b; j++)
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
         };
         if (zhi - zlo <= 1 && yhi - ylo <= 1) {
             // the usual box (2 * rmax below the cell edge): at most 2 x 2 rows,
