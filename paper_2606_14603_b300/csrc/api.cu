@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -714,19 +715,18 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     if (!b || !sim_id) return ABM_EINVAL;
     if (b->failed) return ABM_ESTATE;
     *sim_id = -1;
-    Compiled* c = new (std::nothrow) Compiled();
+    std::unique_ptr<Compiled> c_owner(new (std::nothrow) Compiled());
+    Compiled* c = c_owner.get();
     if (!c) return ABM_ENOMEM;
     std::string msg;
     abm_status st = compile_model(model, c, &msg);
     if (st != ABM_OK) {
         b->err = msg;  // invalid input does not fail the batch
-        delete c;
         return st;
     }
     const uint32_t shift = cell_log2 ? cell_log2 : auto_shift(*c);
     if (shift > 30 || (1ll << shift) < c->Rmax) {
         b->err = "grid cell smaller than a reaction radius";
-        delete c;
         return ABM_EINVAL;
     }
     const uint64_t ncell = cells_for(*c, shift);
@@ -735,7 +735,6 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
         st = restore_set(*c, rec, n_rec, step, next_id, &rs, &msg);
         if (st != ABM_OK) {
             b->err = msg;
-            delete c;
             return st;
         }
         c->n0 = rs.pm.size();  // agents to place
@@ -743,7 +742,6 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     Ctl h;
     st = sync_and_check(b, &h);
     if (st != ABM_OK) {
-        delete c;
         return st;
     }
     auto free_slot = [&]() -> int32_t {
@@ -759,7 +757,6 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     if (draining && (slot < 0 || (uint64_t)h.n_in + c->n0 > b->cap_agents)) {
         st = compact(b, &h);
         if (st != ABM_OK) {
-            delete c;
             return st;
         }
         slot = free_slot();
@@ -767,7 +764,6 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     if (slot < 0 || cells_in_use(b) + ncell > b->cap_cells || (uint64_t)h.n_in + c->n0 > b->cap_agents) {
         b->err = slot < 0 ? "no free simulation slot"
                  : cells_in_use(b) + ncell > b->cap_cells ? "grid cells exhausted" : "agent capacity exhausted";
-        delete c;
         return ABM_ECAPACITY;
     }
     // model table: reuse an identical upload
@@ -829,7 +825,6 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     const uint32_t n_in = h.n_in + (uint32_t)c->n0;
     CU(cudaMemcpyAsync(&b->B.ctl->n_in, &n_in, 4, cudaMemcpyHostToDevice, b->stream));
     st = repack_cells(b);  // synchronises (host temporaries above stay alive until then)
-    delete c;
     if (st != ABM_OK) return st;
     st = sync_and_check(b);
     if (st != ABM_OK) return st;
@@ -1116,7 +1111,8 @@ void abm_batch_destroy(abm_batch* b) {
 
 // ---------------- single simulation = a batch of one ----------------
 size_t abm_arena_bytes(const abm_model* model, const abm_options* opt) {
-    Compiled* c = new (std::nothrow) Compiled();
+    std::unique_ptr<Compiled> c_owner(new (std::nothrow) Compiled());
+    Compiled* c = c_owner.get();
     if (!c) return 0;
     std::string msg;
     size_t bytes = 0;
@@ -1130,13 +1126,13 @@ size_t abm_arena_bytes(const abm_model* model, const abm_options* opt) {
         o.births_per_step = opt ? opt->births_per_step : 0;
         bytes = abm_batch_arena_bytes(&o);
     }
-    delete c;
     return bytes;
 }
 
 abm_status abm_model_grid(const abm_model* model, uint32_t cell_log2, uint32_t* shift_out, uint64_t* cells_out) {
     if (!shift_out || !cells_out) return ABM_EINVAL;
-    Compiled* c = new (std::nothrow) Compiled();
+    std::unique_ptr<Compiled> c_owner(new (std::nothrow) Compiled());
+    Compiled* c = c_owner.get();
     if (!c) return ABM_ENOMEM;
     std::string msg;
     abm_status st = compile_model(model, c, &msg);
@@ -1149,14 +1145,14 @@ abm_status abm_model_grid(const abm_model* model, uint32_t cell_log2, uint32_t* 
             *cells_out = cells_for(*c, shift);
         }
     }
-    delete c;
     return st;
 }
 
 abm_status abm_create(const abm_model* model, uint64_t seed, const abm_options* opt, abm_sim** out) {
     if (!out) return ABM_EINVAL;
     *out = nullptr;
-    Compiled* c = new (std::nothrow) Compiled();
+    std::unique_ptr<Compiled> c_owner(new (std::nothrow) Compiled());
+    Compiled* c = c_owner.get();
     if (!c) return ABM_ENOMEM;
     std::string msg;
     abm_status st = compile_model(model, c, &msg);
@@ -1164,7 +1160,6 @@ abm_status abm_create(const abm_model* model, uint64_t seed, const abm_options* 
     const uint64_t n0 = c->n0;
     const uint64_t cells = st == ABM_OK ? cells_for(*c, shift) : 0;
     const bool small_cell = st == ABM_OK && (1ll << shift) < c->Rmax;
-    delete c;
     if (st != ABM_OK || small_cell || shift > 30) return ABM_EINVAL;
     abm_batch_options o{};
     o.capacity_agents = opt && opt->capacity_agents ? opt->capacity_agents : n0 + n0 / 4 + 65536;
@@ -1200,14 +1195,14 @@ abm_status abm_restore(const abm_model* model, uint64_t seed, const abm_options*
                        size_t n_records, uint32_t step, uint32_t next_id, abm_sim** out) {
     if (!out || (n_records && !records)) return ABM_EINVAL;
     *out = nullptr;
-    Compiled* c = new (std::nothrow) Compiled();
+    std::unique_ptr<Compiled> c_owner(new (std::nothrow) Compiled());
+    Compiled* c = c_owner.get();
     if (!c) return ABM_ENOMEM;
     std::string msg;
     abm_status st = compile_model(model, c, &msg);
     const uint32_t shift = st == ABM_OK ? (opt && opt->cell_log2 ? opt->cell_log2 : auto_shift(*c)) : 0;
     const uint64_t cells = st == ABM_OK ? cells_for(*c, shift) : 0;
     const bool small_cell = st == ABM_OK && (1ll << shift) < c->Rmax;
-    delete c;
     if (st != ABM_OK || small_cell || shift > 30) return ABM_EINVAL;
     abm_batch_options o{};
     o.capacity_agents = opt && opt->capacity_agents ? opt->capacity_agents : n_records + n_records / 4 + 65536;
