@@ -14,8 +14,9 @@
  * One step of every simulation runs: first-order events (release of bound
  * complexes, conversion/degradation, expression), a Brownian move with
  * reflecting walls, rejecting spherical walls and membrane crossing, a cell
- * grid rebuilt by histogram / exclusive scan / scatter, a 27-cell proximity
- * proposal, a nearest-partner handshake (atomicMin on a packed (dist^2, id)
+ * grid rebuilt by histogram / exclusive scan / scatter, a proximity proposal
+ * over the cells a contact radius can reach (the 27-cell neighbourhood pruned
+ * to the reachable cells), a nearest-partner handshake (atomicMin on a packed (dist^2, id)
  * key), reaction application and births.  All state is integer; all
  * randomness is Philox4x32-10 keyed by (seed, step, agent id), so a run is
  * bit-reproducible and independent of storage order.
@@ -28,9 +29,10 @@
  *    ownership.  Device memory passed as `arena` and the `stream` belong to
  *    the caller and must outlive the handle.
  *  - abm_*_step only enqueues work on the stream and returns.  Errors found
- *    on the device (capacity exceeded, bounded waits timed out) are sticky
- *    and reported by the next synchronising call (counts, digest, dump,
- *    sync).
+ *    on the device (capacities exceeded, id space exhausted) are sticky and
+ *    reported by the next synchronising call (counts, digest, dump, sync,
+ *    monitor read).  No call waits on the device beyond a stream
+ *    synchronisation.
  *  - Not thread-safe: one host thread per handle at a time.
  */
 #ifndef ABM_H
