@@ -59,6 +59,8 @@ def lib():
         L.orc_step_index.restype = C.c_uint32
         L.orc_step_index.argtypes = [C.c_void_p]
         L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_set_table.restype = C.c_int
+        L.orc_set_table.argtypes = [C.c_void_p, C.POINTER(C.c_int16)]
         L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.orc_ncdf_table.argtypes = [C.POINTER(C.c_int16)]
         L.orc_gauss_step.restype = C.c_int64
@@ -92,7 +94,7 @@ class OracleError(ValueError):
 class OracleSim:
     """Serial simulator of one model; ids ascending, every phase a plain loop."""
 
-    def __init__(self, model, seed: int, brute_force: bool = False):
+    def __init__(self, model, seed: int, brute_force: bool = False, table=None):
         L = lib()
         sp, rx, cm = _structs(model)
         err = C.create_string_buffer(256)
@@ -102,6 +104,13 @@ class OracleSim:
         if not h:
             raise OracleError(err.value.decode())
         self._h = h
+        if table is not None:  # a caller's Gaussian table (data, like the default one)
+            self._table = np.ascontiguousarray(table, dtype=np.int16)
+            assert self._table.shape == (65536,)
+            if L.orc_set_table(h, self._table.ctypes.data_as(C.POINTER(C.c_int16))) != 0:
+                L.orc_destroy(h)
+                self._h = None
+                raise OracleError("diffusion step exceeds the domain with this table")
         self.model = model
         self.n_species = len(model.species)
         self.n_comp = len(model.compartments)

@@ -655,3 +655,12 @@ size_t orc_dump(const orc_sim* s, orc_record* out, size_t cap) {
 
 size_t orc_n_agents(const orc_sim* s) { return s->n; }
 uint32_t orc_step_index(const orc_sim* s) { return s->t; }
+
+int orc_set_table(orc_sim* s, const int16_t* table) {
+    int zmax = 0;
+    for (int i = 0; i < 65536; i++) zmax = abs(table[i]) > zmax ? abs(table[i]) : zmax;
+    for (int i = 0; i < s->n_sp; i++)
+        if ((int64_t)(((uint64_t)zmax * s->M[i] + 0x80000000ull) >> 32) > s->ext) return -1;
+    memcpy(s->Z, table, sizeof(s->Z));
+    return 0;
+}

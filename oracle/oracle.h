@@ -75,6 +75,10 @@ uint64_t orc_digest(const orc_sim* s);
 size_t   orc_dump(const orc_sim* s, orc_record* out, size_t cap);
 size_t   orc_n_agents(const orc_sim* s);
 uint32_t orc_step_index(const orc_sim* s);
+/* Replace the Gaussian table before the first step (the table is data, and
+   the caller may supply its own).  Returns 0, or -1 when the largest entry
+   would step past the domain, in which case the table is left unchanged. */
+int      orc_set_table(orc_sim* s, const int16_t* table65536);
 void     orc_destroy(orc_sim* s);
 
 /* Building blocks exposed for the pins. */

@@ -91,6 +91,33 @@ def test_toy_one_launch_of_all_steps(A, oracle_mod):
     o.close()
 
 
+@pytest.mark.parametrize("kind", ["antisymmetric", "skewed"])
+def test_caller_gaussian_table(A, oracle_mod, kind):
+    """A caller's Gaussian table (abm_options.ncdf_table), antisymmetric like
+    the default one or not, gives the oracle's results with that table."""
+    base = oracle_mod.ncdf_table()
+    if kind == "antisymmetric":
+        tab = np.trunc(base.astype(np.float64) * 1.5).astype(np.int16)
+        assert np.array_equal(tab[::-1], -tab)
+    else:
+        tab = base.copy()
+        tab[::97] += 1
+        assert not np.array_equal(tab[::-1], -tab)
+    for m, seed, steps in [(W.toy(700, 600, edge_um=0.45), 31, 60), (W.mapk(20_000), 32, 40)]:
+        g = A.Sim(m, seed, ncdf_table=tab)
+        o = oracle_mod.OracleSim(m, seed, table=tab)
+        ref = oracle_mod.OracleSim(m, seed)
+        for _ in range(4):
+            g.step(steps // 4)
+            o.step(steps // 4)
+            ref.step(steps // 4)
+            assert g.digest() == o.digest(), (kind, m.name, g.t)
+        assert o.digest() != ref.digest()  # the table was used
+        assert_same_dump(g.dump(), o.dump(), f"{kind} {m.name}")
+        for x in (g, o, ref):
+            x.close()
+
+
 def test_mapk_scaled_parity(A, oracle_mod):
     c = _lockstep(A, oracle_mod, W.mapk(30_000), W.MAPK_SEED, 400, dump_every=100, digest_every=4)
     assert c[9:-1].sum() > 0                                  # complexes present
