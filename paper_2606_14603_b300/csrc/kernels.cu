@@ -31,7 +31,6 @@ namespace abm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kScanV = kScanTile / kThreads;  // 32 cells per thread
 
 // Programmatic dependent launch: a step kernel may be launched while its
 // predecessor finishes; it waits here until the predecessor's grid has
@@ -422,48 +421,58 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(Buffers B) {
 }
 
 // One scan tile: start[c] = agents in the tiles before + the tile's own
-// exclusive prefix; its counts are reset to zero for the next step.  The
-// agents before the tile are `prefix` plus, when pre_n > 0, the counts of
-// tiles [pre_first, pre_first + pre_n) added up here after this tile's own
-// counts have been requested, so that both sets of loads are in flight at
-// once.  Returns the agents before the next tile.
+// exclusive prefix; its counts are reset to zero for the next step.  Warp w
+// takes the tile's w-th 1024 cells as 8 rows of 128, lane l cells 4l..4l+3
+// of each row, so that every load and store of a warp is 512 contiguous
+// bytes.  The agents before the tile are `prefix` plus, when pre_n > 0, the
+// counts of tiles [pre_first, pre_first + pre_n) added up here after this
+// tile's own counts have been requested, so that both sets of loads are in
+// flight at once.  Returns the agents before the next tile.
 __device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_t prefix, uint32_t pre_first,
                                               uint32_t pre_n, uint32_t* s_warp) {
-    const uint32_t base = tile * kScanTile + threadIdx.x * kScanV;
-    uint32_t v[kScanV];
-    uint4* src = reinterpret_cast<uint4*>(B.cnt + base);
+    constexpr uint32_t kRows = kScanTile / kThreads / 4;  // rows of 128 cells per warp
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t base = tile * kScanTile + warp * (kScanTile / (kThreads / 32)) + lane * 4;
+    uint4* src = reinterpret_cast<uint4*>(B.cnt + base);  // row k at src + 32 k
+    uint4 v[kRows];
 #pragma unroll
-    for (int k = 0; k < kScanV / 4; k++) {
-        const uint4 u = src[k];
-        v[4 * k] = u.x;
-        v[4 * k + 1] = u.y;
-        v[4 * k + 2] = u.z;
-        v[4 * k + 3] = u.w;
-    }
+    for (uint32_t k = 0; k < kRows; k++) v[k] = src[32 * k];
     uint32_t pre_v = 0;
     for (uint32_t t = pre_first + threadIdx.x; t < pre_first + pre_n; t += blockDim.x)
         pre_v += B.tcnt[t * kTileStride];
 #pragma unroll
-    for (int k = 0; k < kScanV / 4; k++) src[k] = make_uint4(0, 0, 0, 0);
-    uint32_t tsum = 0;
+    for (uint32_t k = 0; k < kRows; k++) src[32 * k] = make_uint4(0, 0, 0, 0);
+    // exclusive prefix of each lane's four cells within the warp's rows
+    uint32_t off[kRows], wtot = 0;
 #pragma unroll
-    for (int k = 0; k < kScanV; k++) tsum += v[k];
+    for (uint32_t k = 0; k < kRows; k++) {
+        const uint32_t r = v[k].x + v[k].y + v[k].z + v[k].w;
+        uint32_t incl = r;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        off[k] = wtot + incl - r;
+        wtot += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
     if (pre_n) {
         uint32_t pre_total;
         block_exclusive_scan(pre_v, s_warp, &pre_total);
         prefix += pre_total;
     }
     uint32_t total;
-    uint32_t run = prefix + block_exclusive_scan(tsum, s_warp, &total);
+    const uint32_t wpre = __shfl_sync(0xFFFFFFFFu, block_exclusive_scan(lane == 0 ? wtot : 0u, s_warp, &total), 0);
+    const uint32_t run = prefix + wpre;
     uint4* dst = reinterpret_cast<uint4*>(B.start + base);
 #pragma unroll
-    for (int k = 0; k < kScanV / 4; k++) {
+    for (uint32_t k = 0; k < kRows; k++) {
         uint4 o;
-        o.x = run; run += v[4 * k];
-        o.y = run; run += v[4 * k + 1];
-        o.z = run; run += v[4 * k + 2];
-        o.w = run; run += v[4 * k + 3];
-        dst[k] = o;
+        o.x = run + off[k];
+        o.y = o.x + v[k].x;
+        o.z = o.y + v[k].y;
+        o.w = o.z + v[k].z;
+        dst[32 * k] = o;
     }
     return prefix + total;
 }
