@@ -253,8 +253,8 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
     const size_t sizes[] = {
         16 * C, 16 * C,                        // pm[2]
         4 * C, 4 * C, 4 * C, 4 * C,            // aid[2], apar[2]
-        8 * C, 8 * C, 8 * C, (size_t)C,        // kr, acc, props, pflag
-        16 * E, 4 * E, 8 * E,                  // extras
+        4 * C, 8 * C, 8 * C, (size_t)C,        // rk, acc, props, pflag
+        16 * E, 4 * E, 4 * E,                  // extras
         16 * (size_t)Bc, 4 * (size_t)Bc,       // births
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
         4 * kTileStride * tiles,               // tile counts (one per 128-byte line)
@@ -538,13 +538,13 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.aid[1] = (uint32_t*)at();
     B.apar[0] = (uint32_t*)at();
     B.apar[1] = (uint32_t*)at();
-    B.kr = (uint64_t*)at();
+    B.rk = (uint32_t*)at();
     B.acc = (uint64_t*)at();
     B.props = (uint2*)at();
     B.pflag = (uint8_t*)at();
     B.xpm = (int4*)at();
     B.xid = (uint32_t*)at();
-    B.xkr = (uint64_t*)at();
+    B.xrk = (uint32_t*)at();
     B.bpm = (int4*)at();
     B.bpar = (uint32_t*)at();
     B.cnt = (uint32_t*)at();

@@ -4,11 +4,12 @@
 //   pm[2][C]     int4 {x, y, z, meta}   agent record, double-buffered
 //   aid[2][C]    u32 agent id           (ids are per simulation)
 //   apar[2][C]   u32 partner id         (valid for carriers only)
-//   kr[C]        u64 (cell << 32 | rank within cell) from the move pass
+//   rk[C]        u32 rank within the new cell, from the move pass (the
+//                scatter finds the cell again from the moved record)
 //   acc[C]       u64 proposal slot, min of (dist^2 << 32 | proposer id)
 //   props[C]     (proposer, target) sorted indices of this step's proposals
 //   pflag[C]     1 if the sorted agent is a free proposer (written by the scatter)
-//   xpm/xid/xkr  released partners appended by the move pass (C/2 + 1)
+//   xpm/xid/xrk  released partners appended by the move pass (C/2 + 1)
 //   bpm/bpar     births of the step (B)
 //   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
 //   tcnt[T]      agents per cell tile (8192 cells), counted by the move pass,
@@ -38,7 +39,6 @@ constexpr uint32_t kDirectTiles = 8192;   // up to this many tiles, each scan bl
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kMonTrace = 1024;      // evaluations kept per threshold monitor
 constexpr uint64_t kEmpty = 0xFFFFFFFFFFFFFFFFull;
-constexpr uint64_t kInvalidKey = 0xFFFFFFFFFFFFFFFFull;
 
 constexpr uint32_t M_SP = 0x3Fu;
 constexpr uint32_t M_COMP_SHIFT = 6, M_COMP = 0xC0u;
@@ -146,13 +146,13 @@ struct Buffers {
     int4* pm[2];
     uint32_t* aid[2];
     uint32_t* apar[2];
-    uint64_t* kr;
+    uint32_t* rk;            // per agent: rank within its new cell (kNone: not placed)
     uint64_t* acc;
     uint2* props;
     uint8_t* pflag;
     int4* xpm;
     uint32_t* xid;
-    uint64_t* xkr;
+    uint32_t* xrk;
     int4* bpm;
     uint32_t* bpar;
     uint32_t* cnt;

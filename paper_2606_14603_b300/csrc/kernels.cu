@@ -189,7 +189,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, ui
                     atomicAdd(&B.tcnt[key / kScanTile * kTileStride], 1u);
                     B.xpm[k] = q;
                     B.xid[k] = par;
-                    B.xkr[k] = (uint64_t)key << 32 | rank;
+                    B.xrk[k] = rank;  // the scatter finds the cell again from q
                 } else {
                     raise_error(ctl, ERR_CAPACITY_EXTRAS, k);
                 }
@@ -258,10 +258,10 @@ __device__ __forceinline__ void move_phase2(MoveState& a) {
 __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, const MoveState& a,
                                             uint32_t rank) {
     if (!(a.flags & 1u)) {
-        B.kr[i] = kInvalidKey;
+        B.rk[i] = kNone;
         return;
     }
-    B.kr[i] = (uint64_t)a.key << 32 | rank;
+    B.rk[i] = rank;  // the scatter finds the cell again from the moved record
     B.pm[cur][i] = a.p;
     if (a.flags & 2u) {
         const uint32_t meta = (uint32_t)a.p.w;
@@ -518,30 +518,35 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
     for (uint32_t t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) B.tcnt[t * kTileStride] = 0;
     const uint32_t stride = nb * blockDim.x;
     for (uint32_t j0 = bid * blockDim.x + threadIdx.x; j0 < total; j0 += kScatterILP * stride) {
-        uint64_t kr[kScatterILP];
+        uint32_t rk[kScatterILP];
         int4 p[kScatterILP];
         uint32_t id[kScatterILP], par[kScatterILP];
 #pragma unroll
         for (int u = 0; u < kScatterILP; u++) {
             const uint32_t j = j0 + u * stride;
-            kr[u] = kInvalidKey;
+            rk[u] = kNone;
             par[u] = kNone;
             if (j < n_in) {
-                kr[u] = B.kr[j];
+                rk[u] = B.rk[j];
                 p[u] = B.pm[cur][j];
                 id[u] = B.aid[cur][j];
                 par[u] = B.apar[cur][j];
             } else if (j < total) {
                 const uint32_t k = j - n_in;
-                kr[u] = B.xkr[k];
+                rk[u] = B.xrk[k];
                 p[u] = B.xpm[k];
                 id[u] = B.xid[k];
             }
         }
+        // the cell comes from the moved record, as the move pass computed it
         uint32_t dest[kScatterILP];
 #pragma unroll
-        for (int u = 0; u < kScatterILP; u++)
-            dest[u] = kr[u] == kInvalidKey ? kNone : B.start[kr[u] >> 32] + (uint32_t)kr[u];
+        for (int u = 0; u < kScatterILP; u++) {
+            dest[u] = kNone;
+            if (rk[u] == kNone) continue;
+            const SimDev& S = B.sims[sim_of((uint32_t)p[u].w)];
+            dest[u] = B.start[cell_of(S, p[u].x, p[u].y, p[u].z)] + rk[u];
+        }
 #pragma unroll
         for (int u = 0; u < kScatterILP; u++) {
             if (dest[u] == kNone) continue;
