@@ -1,6 +1,7 @@
 """Longer parity runs, engine vs oracle, bit-exact (digest at checkpoints):
-the 1M-agent cascade for its first 200 steps, a 50k-agent cascade and a
-boosted 40k-agent two-compartment model for 2,000 steps, every simulation of
+the 1M-agent cascade for its first 200 steps, a 50k-agent cascade for the
+cascade's full 10,000 steps, a boosted 40k-agent two-compartment model for
+2,000 steps, every simulation of
 the 64-simulation sweep for its first 100 steps in the batch (the 8 smallest
 to 1,000), and all 64 in the batch against the same simulations run alone
 for 5,000 steps.  (The 4M-agent two-compartment model is checked for 3 steps
@@ -23,7 +24,7 @@ SWEEP = W.sweep()
 SMALLEST = sorted(range(len(SWEEP)), key=lambda k: SWEEP[k][0].n_agents)[:8]
 JOBS = {
     "mapk_1M": ("mapk", {"n_total": 1_000_000}, W.MAPK_SEED, list(range(25, 201, 25))),
-    "mapk_50k": ("mapk", {"n_total": 50_000}, W.MAPK_SEED, list(range(250, 2001, 250))),
+    "mapk_50k": ("mapk", {"n_total": 50_000}, W.MAPK_SEED, list(range(1000, 10_001, 1000))),
     "nuclear_40k": ("nuclear", {"n_total": 40_000, "boost": 100.0, "n_genes": 32, "genes_on": 16},
                     W.NUCLEAR_SEED, list(range(250, 2001, 250))),
 }

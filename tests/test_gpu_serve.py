@@ -2,7 +2,8 @@
 
 Jobs arrive while others are resident; they are admitted as memory and slots
 free up and are stepped together.  Every job's result (counts and digest at
-its last step) must equal the same job run alone, bit for bit."""
+its last step) must equal the same job run alone, bit for bit, and the
+oracle's (the jobs are at most 30k agents x 200 steps)."""
 import numpy as np
 import pytest
 
@@ -25,8 +26,19 @@ def _jobs():
     return [W.Job(k, t, m, s, n) for k, (t, m, s, n) in enumerate(specs)]
 
 
+@pytest.fixture(scope="module")
+def oracle_results(oracle_mod):
+    out = {}
+    for j in _jobs():
+        o = oracle_mod.OracleSim(j.model, j.seed)
+        o.step(j.steps)
+        out[j.job_id] = (o.digest(), o.counts())
+        o.close()
+    return out
+
+
 @pytest.mark.parametrize("groups", [1, 2])
-def test_served_jobs_equal_alone_runs(groups):
+def test_served_jobs_equal_alone_runs(groups, oracle_results):
     require_gpu()
     A = engine()
     from paper_2606_14603_b300 import serve
@@ -49,6 +61,8 @@ def test_served_jobs_equal_alone_runs(groups):
         assert r.digest == alone.digest(), f"job {j.job_id}"
         assert np.array_equal(r.counts, alone.counts()), f"job {j.job_id}"
         alone.close()
+        od, oc = oracle_results[j.job_id]
+        assert r.digest == od and np.array_equal(r.counts, oc), f"job {j.job_id} vs the oracle"
     lat = [r.latency_s for r in out["results"]]
     assert out["latency_p50_s"] <= out["latency_p99_s"] and min(lat) >= 0
 
