@@ -466,28 +466,46 @@ def main():
                  "achieved_gbs": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9,
                  "frac": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9 / hbm}
 
-    # end to end: create from host structs, K steps each followed by a
-    # device-to-host read of the counts vector
+    # end to end: create from host structs, K steps, every step's counts
+    # vector read back to the host: pipelined (each step's read queued into a
+    # pinned slot and collected while the next step runs) and, for
+    # comparison, synchronous (abm_counts after every step)
     e2e = None
     if not args.no_e2e:
         Ke = max(1, min(K, 500))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s2 = A.Sim(model, seed, stream=stream)
-        cvec = None
-        for _ in range(Ke):
-            s2.step(1)
-            cvec = s2.counts()
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        s2.close()
+
+        def e2e_run(pipelined):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = A.Sim(model, seed, stream=stream)
+            cvec = None
+            for k in range(Ke):
+                s2.step(1)
+                if pipelined:
+                    s2.counts_begin(k % 2)
+                    if k:
+                        cvec = s2.counts_finish((k - 1) % 2)
+                else:
+                    cvec = s2.counts()
+            if pipelined:
+                cvec = s2.counts_finish((Ke - 1) % 2)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            s2.close()
+            return cvec, el
+
+        cvec, el = e2e_run(True)
+        cvec_s, el_s = e2e_run(False)
+        assert np.array_equal(cvec, cvec_s)
         n_counts = len(cvec)
         # host-to-device at creation: Gaussian table, integer model tables, sim entry, control words
         model_bytes = 2 * 65536 + 15376 + 512
         e2e = {"value": molecules(cvec, model) * Ke / el, "unit": UNIT,
                "h2d_bytes_per_step": model_bytes / Ke, "d2h_bytes_per_step": 8 * n_counts,
                "steps": Ke, "includes": "abm_create (model upload, device-side placement) + per step "
-                                       "abm_step + abm_counts read back to host"}
+                                       "abm_step + that step's counts read back to the host "
+                                       "(abm_counts_begin / abm_counts_finish, one step in flight)",
+               "synchronous_value": molecules(cvec_s, model) * Ke / el_s}
 
     sweep = None
     if args.sweep_steps > 0 and args.workload == "cascade" and not args.agents:

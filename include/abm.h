@@ -177,6 +177,9 @@ abm_status  abm_restore(const abm_model* model, uint64_t seed, const abm_options
                         uint32_t next_id, abm_sim** out);
 abm_status  abm_step(abm_sim* sim, uint32_t n);
 abm_status  abm_counts(abm_sim* sim, uint64_t* out, size_t cap, size_t* n_out);
+/* Pipelined counts of one simulation: see abm_batch_counts_begin below. */
+abm_status  abm_counts_begin(abm_sim* sim, uint32_t slot);
+abm_status  abm_counts_finish(abm_sim* sim, uint32_t slot, uint64_t* out, size_t cap, size_t* n_out);
 abm_status  abm_digest(abm_sim* sim, uint64_t* out);
 abm_status  abm_dump(abm_sim* sim, abm_record* out, size_t cap, size_t* n_out);
 abm_status  abm_sync(abm_sim* sim);
@@ -215,6 +218,19 @@ abm_status  abm_batch_digest(abm_batch* b, int32_t sim_id, uint64_t* out);
 abm_status  abm_batch_dump(abm_batch* b, int32_t sim_id, abm_record* out, size_t cap,
                            size_t* n_out);
 abm_status  abm_batch_sync(abm_batch* b);
+/* Pipelined counts (the readout of Sec. 2, at every step if wanted, without
+ * stalling the device): _begin queues the count pass for the state after the
+ * steps issued so far and its copy into pinned host slot `slot` (0 ..
+ * ABM_READ_SLOTS - 1) and returns at once; _finish waits for that slot and
+ * writes the counts (layout as abm_batch_counts) to out[0..cap).  A caller
+ * that steps, begins slot k % 2 and finishes slot (k - 1) % 2 keeps the
+ * device busy while it reads.  ABM_EINVAL for a bad slot, _begin on a slot
+ * that is not finished, _finish on one that was not begun, or cap below the
+ * count; device errors surface at _finish as in abm_batch_counts. */
+#define ABM_READ_SLOTS 4
+abm_status  abm_batch_counts_begin(abm_batch* b, int32_t sim_id, uint32_t slot);
+abm_status  abm_batch_counts_finish(abm_batch* b, uint32_t slot, uint64_t* out, size_t cap,
+                                    size_t* n_out);
 abm_status  abm_batch_live_agents(abm_batch* b, uint64_t* out);  /* syncs */
 const char* abm_batch_last_error(const abm_batch* b);
 void        abm_batch_destroy(abm_batch* b);  /* NULL-safe */

@@ -16,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libabm.so")
+READ_SLOTS = 4  # pinned slots of the pipelined counts reads (ABM_READ_SLOTS)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EDEVICE, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 _NAMES = {0: "ABM_OK", -1: "ABM_EINVAL", -2: "ABM_ENOMEM", -3: "ABM_ECUDA", -4: "ABM_ETIMEOUT",
@@ -115,6 +116,8 @@ def lib():
                                             C.c_uint32, C.c_uint32, C.POINTER(C.c_int32)]),
             "abm_step": (C.c_int, [P, C.c_uint32]),
             "abm_counts": (C.c_int, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "abm_counts_begin": (C.c_int, [P, C.c_uint32]),
+            "abm_counts_finish": (C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_digest": (C.c_int, [P, C.POINTER(C.c_uint64)]),
             "abm_dump": (C.c_int, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_sync": (C.c_int, [P]),
@@ -128,6 +131,8 @@ def lib():
             "abm_batch_set_max_step": (C.c_int, [P, C.c_int32, C.c_uint32]),
             "abm_batch_step": (C.c_int, [P, C.c_uint32]),
             "abm_batch_counts": (C.c_int, [P, C.c_int32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "abm_batch_counts_begin": (C.c_int, [P, C.c_int32, C.c_uint32]),
+            "abm_batch_counts_finish": (C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_batch_digest": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
             "abm_batch_dump": (C.c_int, [P, C.c_int32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_batch_sync": (C.c_int, [P]),
@@ -302,6 +307,19 @@ class Sim:
         _check(lib().abm_counts(self._h, out.ctypes.data, out.size, C.byref(n)), lib().abm_last_error, self._h)
         return out
 
+    def counts_begin(self, slot: int = 0) -> None:
+        """Queue a counts read of the state after the steps issued so far into
+        pinned slot `slot` (0..READ_SLOTS-1); returns at once."""
+        _check(lib().abm_counts_begin(self._h, slot), lib().abm_last_error, self._h)
+
+    def counts_finish(self, slot: int = 0) -> np.ndarray:
+        """Wait for the counts read queued in `slot` and return them."""
+        out = np.zeros(self.n_counts, dtype=np.uint64)
+        n = C.c_size_t()
+        _check(lib().abm_counts_finish(self._h, slot, out.ctypes.data, out.size, C.byref(n)),
+               lib().abm_last_error, self._h)
+        return out
+
     def digest(self) -> int:
         v = C.c_uint64()
         _check(lib().abm_digest(self._h, C.byref(v)), lib().abm_last_error, self._h)
@@ -391,6 +409,7 @@ class Batch:
             raise AbmError(st, "abm_batch_create failed")
         self._h = h
         self._n_counts = {}
+        self._read_sims = {}  # pipelined counts reads in flight: slot -> simulation
 
     @staticmethod
     def arena_bytes(capacity_agents: int, capacity_cells: int, max_sims: int, births_per_step: int = 0) -> int:
@@ -430,6 +449,20 @@ class Batch:
         _check(lib().abm_batch_counts(self._h, sim, out.ctypes.data, out.size, C.byref(n)),
                lib().abm_batch_last_error, self._h)
         return out
+
+    def counts_begin(self, sim: int, slot: int = 0) -> None:
+        """Queue a counts read of simulation `sim` into pinned slot `slot`."""
+        _check(lib().abm_batch_counts_begin(self._h, sim, slot), lib().abm_batch_last_error, self._h)
+        self._read_sims[slot] = sim
+
+    def counts_finish(self, slot: int = 0) -> np.ndarray:
+        """Wait for the counts read queued in `slot` and return them."""
+        sim = self._read_sims.pop(slot, None)
+        out = np.zeros(self._n_counts[sim] if sim is not None else 512, dtype=np.uint64)
+        n = C.c_size_t()
+        _check(lib().abm_batch_counts_finish(self._h, slot, out.ctypes.data, out.size, C.byref(n)),
+               lib().abm_batch_last_error, self._h)
+        return out[: n.value]
 
     def digest(self, sim: int) -> int:
         v = C.c_uint64()

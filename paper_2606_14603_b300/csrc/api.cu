@@ -295,6 +295,13 @@ struct abm_batch {
     uint32_t* staging = nullptr;
     Ctl* h_ctl = nullptr;                // pinned host copies: control block ...
     uint64_t* h_counts = nullptr;        // ... and one simulation's counts (512 words)
+    struct ReadSlot {                    // pipelined counts reads
+        uint64_t* host = nullptr;        // pinned: 512 counts, then a copy of the control block
+        cudaEvent_t done = nullptr;
+        uint32_t n = 0;
+        bool pending = false;
+    };
+    ReadSlot rs[ABM_READ_SLOTS];
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;
     struct HostSim {
         int state = 0;  // 0 free, 1 active, 2 draining (removed, not yet stepped)
@@ -369,12 +376,7 @@ abm_status check_device(std::string* msg) {
 }
 
 // Map the sticky device error word to a status.
-abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
-    if (b->failed) return ABM_ESTATE;
-    CU(cudaMemcpyAsync(b->h_ctl, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
-    CU(cudaStreamSynchronize(b->stream));
-    const Ctl h = *b->h_ctl;
-    if (out_ctl) *out_ctl = h;
+abm_status check_ctl(abm_batch* b, const Ctl& h) {
     if (h.err == ERR_NONE) return ABM_OK;
     char buf[160];
     abm_status st = ABM_ECAPACITY;
@@ -389,6 +391,15 @@ abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
     }
     std::snprintf(buf, sizeof buf, "%s (code %u, info %u)", what, h.err, h.err_info);
     return fail(b, st, buf);
+}
+
+abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
+    if (b->failed) return ABM_ESTATE;
+    CU(cudaMemcpyAsync(b->h_ctl, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    const Ctl h = *b->h_ctl;
+    if (out_ctl) *out_ctl = h;
+    return check_ctl(b, h);
 }
 
 abm_status capture(abm_batch* b) {
@@ -528,6 +539,12 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
         cudaGetLastError();
         return destroy_and(ABM_ENOMEM);
     }
+    for (auto& r : b->rs)
+        if (cudaMallocHost((void**)&r.host, 8 * 512 + sizeof(Ctl)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return destroy_and(ABM_ENOMEM);
+        }
     char* a = b->arena;
     int k = 0;
     auto at = [&](void) { return (void*)(a + lay.off[k++]); };
@@ -1038,6 +1055,36 @@ abm_status abm_batch_counts(abm_batch* b, int32_t sim, uint64_t* out, size_t cap
     return st;
 }
 
+abm_status abm_batch_counts_begin(abm_batch* b, int32_t sim, uint32_t slot) {
+    if (!b || slot >= ABM_READ_SLOTS || b->rs[slot].pending) return ABM_EINVAL;
+    abm_status st = observe(b, sim, 0);
+    if (st != ABM_OK) return st;
+    auto& r = b->rs[slot];
+    r.n = b->sims[sim].n_counts;
+    // stream order keeps a later read's reset of the counts behind this copy
+    CU(cudaMemcpyAsync(r.host, b->B.counts + (size_t)sim * 512, 8 * (size_t)r.n, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CU(cudaMemcpyAsync(r.host + 512, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaEventRecord(r.done, b->stream));
+    r.pending = true;
+    return ABM_OK;
+}
+
+abm_status abm_batch_counts_finish(abm_batch* b, uint32_t slot, uint64_t* out, size_t cap, size_t* n_out) {
+    if (!b || slot >= ABM_READ_SLOTS || !b->rs[slot].pending) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    auto& r = b->rs[slot];
+    r.pending = false;
+    CU(cudaEventSynchronize(r.done));
+    Ctl h;
+    std::memcpy(&h, r.host + 512, sizeof(Ctl));
+    abm_status st = check_ctl(b, h);
+    if (st != ABM_OK) return st;
+    if (n_out) *n_out = r.n;
+    if (out && cap) std::memcpy(out, r.host, 8 * std::min<size_t>(cap, r.n));
+    return out && cap < r.n ? ABM_EINVAL : ABM_OK;
+}
+
 abm_status abm_batch_digest(abm_batch* b, int32_t sim, uint64_t* out) {
     if (!b || !out) return ABM_EINVAL;
     abm_status st = observe(b, sim, 1);
@@ -1106,6 +1153,10 @@ void abm_batch_destroy(abm_batch* b) {
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     if (b->h_counts) cudaFreeHost(b->h_counts);
+    for (auto& r : b->rs) {
+        if (r.host) cudaFreeHost(r.host);
+        if (r.done) cudaEventDestroy(r.done);
+    }
     delete b;
 }
 
@@ -1236,6 +1287,12 @@ abm_status abm_restore(const abm_model* model, uint64_t seed, const abm_options*
 abm_status abm_step(abm_sim* s, uint32_t n) { return s ? abm_batch_step(s->b, n) : ABM_EINVAL; }
 abm_status abm_counts(abm_sim* s, uint64_t* out, size_t cap, size_t* n_out) {
     return s ? abm_batch_counts(s->b, s->id, out, cap, n_out) : ABM_EINVAL;
+}
+abm_status abm_counts_begin(abm_sim* s, uint32_t slot) {
+    return s ? abm_batch_counts_begin(s->b, s->id, slot) : ABM_EINVAL;
+}
+abm_status abm_counts_finish(abm_sim* s, uint32_t slot, uint64_t* out, size_t cap, size_t* n_out) {
+    return s ? abm_batch_counts_finish(s->b, slot, out, cap, n_out) : ABM_EINVAL;
 }
 abm_status abm_digest(abm_sim* s, uint64_t* out) { return s ? abm_batch_digest(s->b, s->id, out) : ABM_EINVAL; }
 abm_status abm_dump(abm_sim* s, abm_record* out, size_t cap, size_t* n_out) {

@@ -898,6 +898,45 @@ __global__ void __launch_bounds__(kThreads) k_init(Buffers B, uint32_t sim, uint
 // Each block owns one contiguous range of the cell-sorted array, so almost
 // all of its agents belong to one simulation: those are counted in a
 // shared-memory histogram and flushed with one atomic per bin.
+__device__ __forceinline__ void observe_one(Buffers& B, uint32_t cur, uint32_t i, const int4& p, int32_t only_sim,
+                                            int want_digest, uint32_t sim0, uint32_t* sh) {
+    const uint32_t meta = (uint32_t)p.w;
+    if (meta & (M_DEAD | M_ABSORBED)) return;
+    const uint32_t s = sim_of(meta);
+    if (only_sim >= 0 && s != (uint32_t)only_sim) return;
+    const SimDev& S = B.sims[s];
+    if (!S.active) return;
+    const ModelDev& Mo = B.models[S.model];
+    const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
+    uint32_t slot;
+    uint64_t h = 0;
+    if (meta & M_BOUND) {
+        const uint32_t r = (meta & M_RXN) >> M_RXN_SHIFT;
+        slot = Mo.n_sp * Mo.n_comp + r;
+        if (want_digest) {
+            const ReactionDev& R = Mo.rx[r];
+            const uint32_t id = B.aid[cur][i];
+            const uint32_t par = B.apar[cur][i];
+            const bool ra = meta & M_ROLE_A;
+            h = record_hash(id, sp, comp, 1u | (ra ? 4u : 0u), r, p.x, p.y, p.z, par);
+            h += record_hash(par, ra ? R.b : R.a, comp, 2u | (ra ? 0u : 4u), r, p.x, p.y, p.z, id);
+        }
+    } else {
+        slot = sp * Mo.n_comp + comp;
+        if (want_digest) h = record_hash(B.aid[cur][i], sp, comp, 0u, 0xFFu, p.x, p.y, p.z, kNone);
+    }
+    if (s == sim0) atomicAdd(&sh[slot], 1u);
+    else atomicAdd((unsigned long long*)&B.counts[S.counts_off + slot], 1ull);
+    if (want_digest) {
+        // reduce over the threads of the same simulation: one atomic each
+        cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), (int)s);
+        const uint64_t sum = cg::reduce(grp, h, cg::plus<uint64_t>());
+        if (grp.thread_rank() == 0) atomicAdd((unsigned long long*)&B.digests[s], (unsigned long long)sum);
+    }
+}
+
+constexpr int kObserveILP = 4;
+
 __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_sim, int want_digest) {
     __shared__ uint32_t sh[512];
     __shared__ uint32_t s_sim;
@@ -916,41 +955,16 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
     }
     __syncthreads();
     const uint32_t sim0 = s_sim;
-    for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
-        const int4 p = B.pm[cur][i];
-        const uint32_t meta = (uint32_t)p.w;
-        if (meta & (M_DEAD | M_ABSORBED)) continue;
-        const uint32_t s = sim_of(meta);
-        if (only_sim >= 0 && s != (uint32_t)only_sim) continue;
-        const SimDev& S = B.sims[s];
-        if (!S.active) continue;
-        const ModelDev& Mo = B.models[S.model];
-        const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
-        uint32_t slot;
-        uint64_t h = 0;
-        if (meta & M_BOUND) {
-            const uint32_t r = (meta & M_RXN) >> M_RXN_SHIFT;
-            slot = Mo.n_sp * Mo.n_comp + r;
-            if (want_digest) {
-                const ReactionDev& R = Mo.rx[r];
-                const uint32_t id = B.aid[cur][i];
-                const uint32_t par = B.apar[cur][i];
-                const bool ra = meta & M_ROLE_A;
-                h = record_hash(id, sp, comp, 1u | (ra ? 4u : 0u), r, p.x, p.y, p.z, par);
-                h += record_hash(par, ra ? R.b : R.a, comp, 2u | (ra ? 0u : 4u), r, p.x, p.y, p.z, id);
-            }
-        } else {
-            slot = sp * Mo.n_comp + comp;
-            if (want_digest) h = record_hash(B.aid[cur][i], sp, comp, 0u, 0xFFu, p.x, p.y, p.z, kNone);
+    // several records per thread, all requested before any is examined
+    for (uint32_t i0 = begin + threadIdx.x; i0 < end; i0 += kObserveILP * blockDim.x) {
+        int4 p[kObserveILP];
+#pragma unroll
+        for (int u = 0; u < kObserveILP; u++) {
+            const uint32_t i = i0 + u * blockDim.x;
+            p[u] = i < end ? B.pm[cur][i] : make_int4(0, 0, 0, (int)M_DEAD);
         }
-        if (s == sim0) atomicAdd(&sh[slot], 1u);
-        else atomicAdd((unsigned long long*)&B.counts[S.counts_off + slot], 1ull);
-        if (want_digest) {
-            // reduce over the threads of the same simulation: one atomic each
-            cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), (int)s);
-            const uint64_t sum = cg::reduce(grp, h, cg::plus<uint64_t>());
-            if (grp.thread_rank() == 0) atomicAdd((unsigned long long*)&B.digests[s], (unsigned long long)sum);
-        }
+#pragma unroll
+        for (int u = 0; u < kObserveILP; u++) observe_one(B, cur, i0 + u * blockDim.x, p[u], only_sim, want_digest, sim0, sh);
     }
     __syncthreads();
     if (sim0 != kNone) {

@@ -36,6 +36,11 @@ def test_exports_every_declared_symbol(A):
         assert hasattr(lib, n), n
 
 
+def test_read_slots_match_the_header(A):
+    src = open(os.path.join(ROOT, "include", "abm.h")).read()
+    assert int(re.search(r"#define ABM_READ_SLOTS (\d+)", src).group(1)) == A.READ_SLOTS
+
+
 def test_version(A):
     assert b"sm_103a" in A.lib().abm_version()
 
