@@ -29,7 +29,7 @@ UNIT = "molecule-steps/s"
 # per-kernel bytes each launch must move per unit (agent or cell) in this
 # design; the step as a whole must read and rewrite the 20-byte agent record
 STEP_BYTES_PER_AGENT = 40
-KERNEL_BYTES = {"k_move": (44, "agent"), "k_tile_prefix": (8 / 8192, "cell"), "k_scan": (12, "cell"),
+KERNEL_BYTES = {"k_move": (40, "agent"), "k_tile_prefix": (8 / 8192, "cell"), "k_scan": (12, "cell"),
                 "k_scatter": (53, "agent"), "k_propose": (24, "agent"), "k_accept": (4, "agent")}
 
 

@@ -155,7 +155,7 @@ __device__ __forceinline__ void monitor_eval(Buffers& B, uint32_t s) {
 
 // Phase 1: P1 events (a released partner is moved and placed right away:
 // rare) and the move draw; issues the three table loads.
-__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, uint32_t par, MoveState& a) {
+__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, MoveState& a) {
     uint32_t meta = (uint32_t)a.p.w;
     a.flags = 0;
     if (meta & (M_DEAD | M_ABSORBED)) return;
@@ -179,6 +179,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t i, ui
             const int hprod = ra ? R.prod_b : R.prod_a;
             meta &= ~(M_BOUND | M_ROLE_A | M_RXN);
             if (hprod >= 0) {  // the partner reappears here and moves on its own
+                const uint32_t par = B.apar[cur][i];  // read only here: few agents are in complexes
                 int4 q = a.p;
                 q.w = (int)with_species(meta, (uint32_t)hprod, Mo);
                 brownian_move(S, Mo.sp[hprod], B.ztab, q, par, t);
@@ -285,7 +286,6 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     if (bid == 0 && threadIdx.x == 0) ctl->n_sorted = 0;  // the scan writes the real count
     const int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
-    const uint32_t* __restrict__ apar = B.apar[cur];
     // proposal slots touched last step become empty again (the list is short)
     const uint32_t np = ctl->n_props;
     const uint32_t stride = nb * blockDim.x;
@@ -307,11 +307,10 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     const uint32_t len = ((n + warps - 1) / warps + 31u) & ~31u;
     const uint32_t wbeg = min(n, w * len), wend = min(n, wbeg + len);
     int4 nx_p = make_int4(0, 0, 0, 0);
-    uint32_t nx_id = 0, nx_par = 0;
+    uint32_t nx_id = 0;
     if (wbeg + lane < wend) {
         nx_p = pm[wbeg + lane];
         nx_id = aid[wbeg + lane];
-        nx_par = apar[wbeg + lane];
     }
     uint32_t run_tile = kNone, run_n = 0;  // the same in every lane
     for (uint32_t base = wbeg; base < wend; base += 32) {  // uniform over the warp
@@ -320,14 +319,12 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
         a.flags = 0;
         a.p = nx_p;
         a.id = nx_id;
-        const uint32_t par = nx_par;
         if (i + 32 < wend) {
             nx_p = pm[i + 32];
             nx_id = aid[i + 32];
-            nx_par = apar[i + 32];
         }
         if (i < wend) {
-            move_phase1(B, ctl, i, par, a);
+            move_phase1(B, ctl, cur, i, a);
             move_phase2(a);
         }
         const uint32_t rank = (a.flags & 1u) ? atomicAdd(&B.cnt[a.key], 1u) : 0u;
