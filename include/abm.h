@@ -30,8 +30,8 @@
  *    the caller and must outlive the handle.
  *  - abm_*_step only enqueues work on the stream and returns.  Errors found
  *    on the device (capacities exceeded, id space exhausted) are sticky and
- *    reported by the next synchronising call (counts, digest, dump, sync,
- *    monitor read).  No call waits on the device beyond a stream
+ *    reported by the next synchronising call (counts, counts_finish, digest,
+ *    dump, sync, monitor read).  No call waits on the device beyond a stream
  *    synchronisation.
  *  - Not thread-safe: one host thread per handle at a time.
  */

@@ -673,7 +673,7 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         Best best;
         uint32_t ida = kNone;
         // x-consecutive cells of one (z, y) row form one contiguous range of
-        // the sorted array; walked two candidate records at a time
+        // the sorted array, walked one candidate record at a time
         auto walk = [&](uint32_t a, uint32_t b) {
             for (uint32_t j = a; j < b; j++)
                 if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
