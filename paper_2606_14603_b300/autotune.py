@@ -50,16 +50,20 @@ def batch_for(sims: Sequence[Tuple[object, int]], cell_delta: int = 0, blocks_pe
 
 
 class BatchGroup:
-    """The simulations split over `groups` batches (round-robin by size, so
-    the groups hold similar agent counts), each on its own CUDA stream and
-    stepped together.  Simulation k of the input keeps index k here."""
+    """The simulations split over `groups` batches (dealt by size in snake
+    order, 0 1 .. G-1 G-1 .. 1 0 ..., so that the groups hold nearly equal
+    agent counts), each on its own CUDA stream and stepped together.
+    Simulation k of the input keeps index k here."""
 
     def __init__(self, sims: Sequence[Tuple[object, int]], cell_delta: int = 0, blocks_per_sm: int = 0,
                  groups: int = 1, headroom: float = 1.25, streams=None):
         import torch
         groups = max(1, min(groups, len(sims)))
         order = sorted(range(len(sims)), key=lambda k: sims[k][0].n_agents)
-        members = [order[g::groups] for g in range(groups)]
+        members = [[] for _ in range(groups)]
+        for r, k in enumerate(order):
+            pos = r % groups
+            members[pos if (r // groups) % 2 == 0 else groups - 1 - pos].append(k)
         self.streams = streams or [torch.cuda.Stream() for _ in range(groups)]
         self.batches, self.where = [], {}
         for g, ks in enumerate(members):
