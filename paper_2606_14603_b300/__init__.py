@@ -458,7 +458,7 @@ class Batch:
     def counts_finish(self, slot: int = 0) -> np.ndarray:
         """Wait for the counts read queued in `slot` and return them."""
         sim = self._read_sims.pop(slot, None)
-        out = np.zeros(self._n_counts[sim] if sim is not None else 512, dtype=np.uint64)
+        out = np.zeros(self._n_counts.get(sim, 512), dtype=np.uint64)  # (the sim may be gone since)
         n = C.c_size_t()
         _check(lib().abm_batch_counts_finish(self._h, slot, out.ctypes.data, out.size, C.byref(n)),
                lib().abm_batch_last_error, self._h)
