@@ -118,6 +118,31 @@ def test_caller_gaussian_table(A, oracle_mod, kind):
             x.close()
 
 
+@pytest.mark.parametrize("mobile", [False, True])
+def test_dense_conflicts(A, oracle_mod, mobile):
+    """About four agents within a contact radius of each: most acceptors are
+    contested and many proposers are proposed to, so the final-edge rule
+    decides most outcomes (the static case is the one the oracle is pinned
+    on by brute force); the mobile case adds moves and releases."""
+    import dataclasses
+    from test_oracle_p5 import _model
+    m = _model()
+    if mobile:
+        m = dataclasses.replace(m, species=[dataclasses.replace(sp, D=d) for sp, d in zip(m.species, [2.0, 1.0, 1.5, 0.5])],
+                                reactions=[dataclasses.replace(r, p_release=0.2) if r.kind == W.BIND else r
+                                           for r in m.reactions])
+    for seed in (5, 6):
+        g = A.Sim(m, seed)
+        o = oracle_mod.OracleSim(m, seed)
+        for t in range(30):
+            g.step(1)
+            o.step(1)
+            assert g.digest() == o.digest(), (mobile, seed, t + 1)
+        assert_same_dump(g.dump(), o.dump(), f"dense mobile={mobile} seed {seed}")
+        g.close()
+        o.close()
+
+
 def test_mapk_scaled_parity(A, oracle_mod):
     c = _lockstep(A, oracle_mod, W.mapk(30_000), W.MAPK_SEED, 400, dump_every=100, digest_every=4)
     assert c[9:-1].sum() > 0                                  # complexes present
