@@ -49,9 +49,9 @@ def _llround(x):
     return int(math.floor(x + 0.5)) if x >= 0 else -int(math.floor(-x + 0.5))
 
 
-def _brute_force_step(oracle_mod, model, seed, rec):
-    """Expected {id: (species or None if gone, flags, partner)} after one step from rec."""
-    t = 0
+def _brute_force_step(oracle_mod, model, seed, rec, t=0):
+    """Expected {id: (species or None if gone, flags, partner, reaction)}
+    after P4 + P5 of step t among the free agents in rec."""
     key = (seed & 0xFFFFFFFF, seed >> 32)
     ids = rec["id"].astype(np.int64)
     sp = rec["sp"].astype(np.int64)
@@ -81,7 +81,7 @@ def _brute_force_step(oracle_mod, model, seed, rec):
     for i, (dd, _, j, _) in best.items():
         if j not in acc or (dd, int(ids[i])) < acc[j][:2]:
             acc[j] = (dd, int(ids[i]), i)
-    out = {int(ids[i]): (int(sp[i]), 0, None) for i in range(n)}
+    out = {int(ids[i]): (int(sp[i]), 0, None, None) for i in range(n)}
     n_final = 0
     for i, (dd, _, j, k) in best.items():
         if acc[j][2] != i or i in acc:  # not the acceptor's choice, or proposed to itself
@@ -90,20 +90,96 @@ def _brute_force_step(oracle_mod, model, seed, rec):
         r = model.reactions[k]
         ia, ib = int(ids[i]), int(ids[j])
         if r.kind == W.CONVERT:
-            out[ia] = (r.prod_a if r.prod_a >= 0 else None, 0, None)
-            out[ib] = (r.prod_b if r.prod_b >= 0 else None, 0, None)
+            out[ia] = (r.prod_a if r.prod_a >= 0 else None, 0, None, None)
+            out[ib] = (r.prod_b if r.prod_b >= 0 else None, 0, None, None)
         else:
             Da, Db = model.species[sp[i]].D, model.species[sp[j]].D
             if Da <= Db:  # the proposer carries (ties included)
-                out[ia] = (int(sp[i]), 1 | 4, ib)
-                out[ib] = (int(sp[j]), 2, ia)
+                out[ia] = (int(sp[i]), 1 | 4, ib, k)
+                out[ib] = (int(sp[j]), 2, ia, k)
             else:
-                out[ib] = (int(sp[j]), 1, ia)
-                out[ia] = (int(sp[i]), 2 | 4, ib)
+                out[ib] = (int(sp[j]), 1, ia, k)
+                out[ia] = (int(sp[i]), 2 | 4, ib, k)
     stats = {"proposals": len(best), "final": n_final,
              "contested": sum(1 for j in acc if sum(1 for v in best.values() if v[2] == j) > 1),
              "blocked": sum(1 for i in best if i in acc)}
     return out, stats
+
+
+def _state(rec):
+    return {int(r["id"]): {"sp": int(r["sp"]), "comp": int(r["comp"]), "flags": int(r["flags"]),
+                           "partner": int(r["partner"]), "rxn": int(r["rxn"]),
+                           "pos": (int(r["x"]), int(r["y"]), int(r["z"]))} for r in rec}
+
+
+def _release_then_pair(oracle_mod, model, seed, state, t):
+    """One step of immobile agents from `state` (possibly with complexes):
+    P1 releases (a carrier draws e = Philox(ctr = (id, t, 1, 0)) and lets go
+    iff e[0] < floor(p_release * 2^32); the carrier takes its reaction's
+    product for its role and the hidden partner the other, at the carrier's
+    place, both free), then P4 + P5 among the free agents."""
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    st = {i: dict(a) for i, a in state.items()}
+    n_released = 0
+    for i in sorted(st):
+        a = st[i]
+        if not a["flags"] & 1:
+            continue  # only carriers draw (hidden partners have no events)
+        r = model.reactions[a["rxn"]]
+        if oracle_mod.philox4x32_10((i, t, 1, 0), key)[0] >= oracle_mod.threshold(r.p_release):
+            continue
+        h = st[a["partner"]]
+        carrier_is_a = bool(a["flags"] & 4)
+        a_prod, h_prod = (r.prod_a, r.prod_b) if carrier_is_a else (r.prod_b, r.prod_a)
+        for x, sp in ((a, a_prod), (h, h_prod)):
+            x.update(sp=sp, flags=0, partner=0xFFFFFFFF, rxn=0xFF)
+        h["pos"], h["comp"] = a["pos"], a["comp"]
+        n_released += 1
+    free = [i for i in sorted(st) if st[i]["flags"] == 0]
+    rec = np.zeros(len(free), dtype=oracle_mod.RECORD_DTYPE)
+    for k, i in enumerate(free):
+        a = st[i]
+        rec[k]["id"], rec[k]["sp"], rec[k]["comp"] = i, a["sp"], a["comp"]
+        rec[k]["x"], rec[k]["y"], rec[k]["z"] = a["pos"]
+    out, stats = _brute_force_step(oracle_mod, model, seed, rec, t)
+    for i, (spc, flags, partner, rxn) in out.items():
+        if spc is None:
+            del st[i]
+            continue
+        st[i]["sp"], st[i]["flags"] = spc, flags
+        if partner is not None:
+            st[i]["partner"], st[i]["rxn"] = partner, rxn
+            carrier = i if flags & 1 else partner
+            st[i]["pos"] = st[carrier]["pos"]
+    stats["released"] = n_released
+    return st, stats
+
+
+def test_two_steps_with_releases(oracle_mod):
+    """Complexes formed in step 1 (the BIND's acceptor becomes C when
+    released) release with probability 1/2 in step 2, and the freed agents
+    take part in that step's proposals."""
+    import dataclasses
+    base = _model()
+    model = dataclasses.replace(base, reactions=[base.reactions[0],
+                                                 W.Reaction(Q, B, W.BIND, Q, C, 4.0, 0.8, 0.5),
+                                                 base.reactions[2]])
+    for seed in (7, 8):
+        o = oracle_mod.OracleSim(model, seed)
+        st = _state(o.dump())
+        released = 0
+        for t in range(3):
+            st, stats = _release_then_pair(oracle_mod, model, seed, st, t)
+            released += stats["released"]
+            o.step(1)
+            got = _state(o.dump())
+            want = {i: {k: v for k, v in a.items() if k != "rxn" and (k != "partner" or a["flags"])}
+                    for i, a in st.items()}
+            got = {i: {k: v for k, v in a.items() if k != "rxn" and (k != "partner" or a["flags"])}
+                   for i, a in got.items()}
+            assert got == want, (seed, t + 1)
+        o.close()
+        assert released >= 10, released
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 11, 12345, 2 ** 40 + 7])
@@ -120,7 +196,7 @@ def test_one_static_step_equals_the_brute_force(oracle_mod, seed):
     got = {int(r["id"]): r for r in after}
     assert set(got) == {i for i, v in want.items() if v[0] is not None}
     pos_of = {int(r["id"]): (int(r["x"]), int(r["y"]), int(r["z"])) for r in before}
-    for i, (spc, flags, partner) in want.items():
+    for i, (spc, flags, partner, _) in want.items():
         if spc is None:
             continue
         r = got[i]
