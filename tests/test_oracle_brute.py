@@ -1,5 +1,6 @@
-"""The oracle's first-order events (P1), moves (P2) and births (P6) against
-a per-agent brute force (CPU), a few steps from the initial dump.
+"""The oracle's initial placement, first-order events (P1), moves (P2) and
+births (P6) against a per-agent brute force (CPU), a few steps from the
+initial dump.
 
 The statistical pins (binomial counts, mean squared displacement, wall and
 membrane equilibria) fix rates and laws; these fix every draw.  Each test
@@ -184,3 +185,38 @@ def test_first_order_events_and_births(oracle_mod, seed):
     assert got == want
     sp = [a[0] for a in got.values()]
     assert sp.count(4) >= 100 and sp.count(1) >= 100 and sp.count(2) < 150  # births, conversions, deaths
+
+
+def _placement(oracle_mod, model, seed):
+    """Initial places: ids species-major; agent id draws
+    w = Philox(ctr = (id, attempt, 0, 2)) for attempt = 0, 1, ... and takes
+    ((w[0] * (L + 1)) >> 32, (w[1] * (L + 1)) >> 32, (w[2] * (L + 1)) >> 32)
+    at the first attempt that lies in its species' compartment."""
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    geo = _Geo(model)
+    out, i = {}, 0
+    for s, sp in enumerate(model.species):
+        for _ in range(sp.count):
+            for attempt in range(1 << 16):
+                w = oracle_mod.philox4x32_10((i, attempt, 0, 2), key)
+                p = [(w[d] * (geo.L + 1)) >> 32 for d in range(3)]
+                if geo.locate(p) == sp.comp:
+                    out[i] = [s, sp.comp] + p
+                    break
+            i += 1
+    return out
+
+
+@pytest.mark.parametrize("seed", [1, 2 ** 36 + 3])
+def test_initial_placement(oracle_mod, seed):
+    cell = W.Compartment(W.SPHERE, 0.3)
+    nucleus = W.Compartment(W.SPHERE, 0.15, parent=0, center_um=(0.02, -0.01, 0.0))
+    for model in (W.Model("cube", [W.Species("X", 300, 1.0), W.Species("Y", 200, 1.0)], [],
+                          [W.Compartment(W.CUBE, 0.2)]),
+                  W.Model("cell", [W.Species("P", 400, 1.0, comp=0), W.Species("R", 300, 1.0, comp=1)], [],
+                          [cell, nucleus])):
+        o = oracle_mod.OracleSim(model, seed)
+        got = {int(r["id"]): [int(r["sp"]), int(r["comp"]), int(r["x"]), int(r["y"]), int(r["z"])]
+               for r in o.dump()}
+        o.close()
+        assert got == _placement(oracle_mod, model, seed), model.name
