@@ -143,6 +143,35 @@ def test_dense_conflicts(A, oracle_mod, mobile):
         o.close()
 
 
+def test_brute_force_models(A, oracle_mod):
+    """The small models the oracle is pinned on draw by draw: moves in a cube
+    and in a cell with an off-centre nucleus (rejections, crossings), and
+    first-order events with births; 30 steps, digest every step."""
+    cell = W.Compartment(W.SPHERE, 0.3)
+    nucleus = W.Compartment(W.SPHERE, 0.15, parent=0, center_um=(0.02, -0.01, 0.0))
+    models = [
+        W.Model("cube_moves", [W.Species("X", 300, 3.0), W.Species("Y", 200, 0.6)], [], [W.Compartment(W.CUBE, 0.2)]),
+        W.Model("cell_moves", [W.Species("P", 400, 5.0, comp=0, p_cross=0.5),
+                               W.Species("R", 300, 5.0, comp=1, p_cross=0.0),
+                               W.Species("S", 200, 5.0, comp=1, p_cross=0.5)], [], [cell, nucleus]),
+        W.Model("events", [W.Species("U", 200, 0.0, p_uni=0.3, uni_to=1), W.Species("V", 0, 0.0),
+                           W.Species("Dd", 200, 0.0, p_uni=0.2, uni_to=-1),
+                           W.Species("E", 200, 0.0, p_emit=0.4, emit=4), W.Species("K", 0, 0.0),
+                           W.Species("F", 200, 0.0, p_uni=0.25, uni_to=1, p_emit=0.5, emit=4)], [],
+                [W.Compartment(W.CUBE, 0.3)]),
+    ]
+    for m in models:
+        g = A.Sim(m, 9, births_per_step=1024)
+        o = oracle_mod.OracleSim(m, 9)
+        for t in range(30):
+            g.step(1)
+            o.step(1)
+            assert g.digest() == o.digest(), (m.name, t + 1)
+        assert_same_dump(g.dump(), o.dump(), m.name)
+        g.close()
+        o.close()
+
+
 def test_mapk_scaled_parity(A, oracle_mod):
     c = _lockstep(A, oracle_mod, W.mapk(30_000), W.MAPK_SEED, 400, dump_every=100, digest_every=4)
     assert c[9:-1].sum() > 0                                  # complexes present
