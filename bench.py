@@ -467,9 +467,10 @@ def main():
                  "frac": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9 / hbm}
 
     # end to end: create from host structs, K steps, every step's counts
-    # vector read back to the host: pipelined (each step's read queued into a
-    # pinned slot and collected while the next step runs) and, for
-    # comparison, synchronous (abm_counts after every step)
+    # vector read back to the host: pipelined (the step keeps its result's
+    # counts; each step's copy is queued into a pinned slot and collected while
+    # the next step runs) and, for comparison, synchronous (abm_counts, a
+    # counting pass and a wait, after every step)
     e2e = None
     if not args.no_e2e:
         Ke = max(1, min(K, 500))
@@ -478,6 +479,8 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s2 = A.Sim(model, seed, stream=stream)
+            if pipelined:
+                s2.live_counts(True)  # each step keeps its result's counts: a read is a copy
             cvec = None
             for k in range(Ke):
                 s2.step(1)
@@ -504,7 +507,8 @@ def main():
                "h2d_bytes_per_step": model_bytes / Ke, "d2h_bytes_per_step": 8 * n_counts,
                "steps": Ke, "includes": "abm_create (model upload, device-side placement) + per step "
                                        "abm_step + that step's counts read back to the host "
-                                       "(abm_counts_begin / abm_counts_finish, one step in flight)",
+                                       "(live counts, abm_counts_begin / abm_counts_finish, one step "
+                                       "in flight)",
                "synchronous_value": molecules(cvec_s, model) * Ke / el_s}
 
     sweep = None

@@ -180,6 +180,7 @@ abm_status  abm_counts(abm_sim* sim, uint64_t* out, size_t cap, size_t* n_out);
 /* Pipelined counts of one simulation: see abm_batch_counts_begin below. */
 abm_status  abm_counts_begin(abm_sim* sim, uint32_t slot);
 abm_status  abm_counts_finish(abm_sim* sim, uint32_t slot, uint64_t* out, size_t cap, size_t* n_out);
+abm_status  abm_live_counts(abm_sim* sim, int on);  /* see abm_batch_live_counts */
 abm_status  abm_digest(abm_sim* sim, uint64_t* out);
 abm_status  abm_dump(abm_sim* sim, abm_record* out, size_t cap, size_t* n_out);
 abm_status  abm_sync(abm_sim* sim);
@@ -229,6 +230,15 @@ abm_status  abm_batch_sync(abm_batch* b);
  * count; device errors surface at _finish as in abm_batch_counts. */
 #define ABM_READ_SLOTS 4
 abm_status  abm_batch_counts_begin(abm_batch* b, int32_t sim_id, uint32_t slot);
+/* Live counts (on = 1): every step also leaves the counts of its result in a
+ * device buffer; the move pass counts the moved agents as it writes them, the
+ * acceptance walk and the births add their changes.  abm_batch_counts_begin
+ * then only copies them, with no pass over the agents, whenever a step has
+ * run since live counts were switched on and since the last admission,
+ * restore or removal; otherwise it counts as before.  The values are the same
+ * either way.  Costs one shared-memory add per agent per step while on.
+ * Asynchronous; on = 0 switches it off. */
+abm_status  abm_batch_live_counts(abm_batch* b, int on);
 abm_status  abm_batch_counts_finish(abm_batch* b, uint32_t slot, uint64_t* out, size_t cap,
                                     size_t* n_out);
 abm_status  abm_batch_live_agents(abm_batch* b, uint64_t* out);  /* syncs */

@@ -117,6 +117,7 @@ def lib():
             "abm_step": (C.c_int, [P, C.c_uint32]),
             "abm_counts": (C.c_int, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_counts_begin": (C.c_int, [P, C.c_uint32]),
+            "abm_live_counts": (C.c_int, [P, C.c_int]),
             "abm_counts_finish": (C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_digest": (C.c_int, [P, C.POINTER(C.c_uint64)]),
             "abm_dump": (C.c_int, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -132,6 +133,7 @@ def lib():
             "abm_batch_step": (C.c_int, [P, C.c_uint32]),
             "abm_batch_counts": (C.c_int, [P, C.c_int32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_batch_counts_begin": (C.c_int, [P, C.c_int32, C.c_uint32]),
+            "abm_batch_live_counts": (C.c_int, [P, C.c_int]),
             "abm_batch_counts_finish": (C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_batch_digest": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
             "abm_batch_dump": (C.c_int, [P, C.c_int32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -307,6 +309,11 @@ class Sim:
         _check(lib().abm_counts(self._h, out.ctypes.data, out.size, C.byref(n)), lib().abm_last_error, self._h)
         return out
 
+    def live_counts(self, on: bool = True) -> None:
+        """Every step also keeps the counts of its result (counts_begin then
+        needs no pass over the agents)."""
+        _check(lib().abm_live_counts(self._h, 1 if on else 0), lib().abm_last_error, self._h)
+
     def counts_begin(self, slot: int = 0) -> None:
         """Queue a counts read of the state after the steps issued so far into
         pinned slot `slot` (0..READ_SLOTS-1); returns at once."""
@@ -449,6 +456,11 @@ class Batch:
         _check(lib().abm_batch_counts(self._h, sim, out.ctypes.data, out.size, C.byref(n)),
                lib().abm_batch_last_error, self._h)
         return out
+
+    def live_counts(self, on: bool = True) -> None:
+        """Every step also keeps the counts of its result (counts_begin then
+        needs no pass over the agents)."""
+        _check(lib().abm_batch_live_counts(self._h, 1 if on else 0), lib().abm_batch_last_error, self._h)
 
     def counts_begin(self, sim: int, slot: int = 0) -> None:
         """Queue a counts read of simulation `sim` into pinned slot `slot`."""

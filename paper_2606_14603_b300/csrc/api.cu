@@ -261,6 +261,7 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
         4 * tiles,                             // tile prefixes
         sizeof(SimDev) * S, sizeof(ModelDev) * S,
         8 * (size_t)S * 512, 8 * (size_t)S,    // counts, digests
+        2 * 8 * (size_t)S * 512,               // live counts, by step parity
         sizeof(MonDev) * S, 4 * (size_t)S * 512,   // threshold monitors, their weights
         8 * (size_t)S, 8 * (size_t)S * kMonTrace,  // monitor sums, evaluated values
         2 * 65536,                             // Gaussian table
@@ -302,7 +303,11 @@ struct abm_batch {
         bool pending = false;
     };
     ReadSlot rs[ABM_READ_SLOTS];
+    uint32_t epoch_host = 1;             // device epoch after the steps issued so far
+    uint32_t live_on = 0;                // host copy of ctl.live_counts (source of its upload)
+    bool live_valid = false;             // live counts hold the current state (a step ran with them on)
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+    cudaGraphExec_t g1_live = nullptr, g8_live = nullptr;  // the same with live counts, captured on first use
     struct HostSim {
         int state = 0;  // 0 free, 1 active, 2 draining (removed, not yet stepped)
         uint32_t model_slot = 0;
@@ -402,7 +407,7 @@ abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
     return check_ctl(b, h);
 }
 
-abm_status capture(abm_batch* b) {
+abm_status capture(abm_batch* b, bool live = false) {
     cudaStream_t cs;
     CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     for (int k = 0; k < 2; k++) {
@@ -413,13 +418,14 @@ abm_status capture(abm_batch* b) {
             cudaStreamDestroy(cs);
             return cuda_fail(b, e, "cudaStreamBeginCapture");
         }
-        for (int s = 0; s < steps; s++) launch_step(b->B, b->L, cs);
+        for (int s = 0; s < steps; s++) launch_step(b->B, b->L, cs, live);
         e = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess) {
             cudaStreamDestroy(cs);
             return cuda_fail(b, e, "cudaStreamEndCapture");
         }
-        e = cudaGraphInstantiate(k == 0 ? &b->g1 : &b->g8, graph, 0);
+        cudaGraphExec_t* exec = live ? (k == 0 ? &b->g1_live : &b->g8_live) : (k == 0 ? &b->g1 : &b->g8);
+        e = cudaGraphInstantiate(exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             cudaStreamDestroy(cs);
@@ -572,6 +578,8 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.models = (ModelDev*)at();
     B.counts = (uint64_t*)at();
     B.digests = (uint64_t*)at();
+    B.live = (uint64_t*)at();
+    B.live_stride = b->max_sims * 512u;
     B.mons = (MonDev*)at();
     B.mon_w = (int32_t*)at();
     B.mon_acc = (uint64_t*)at();
@@ -732,6 +740,7 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     if (!b || !sim_id) return ABM_EINVAL;
     if (b->failed) return ABM_ESTATE;
     *sim_id = -1;
+    b->live_valid = false;  // the live counts lack the admitted simulation until a step has run
     std::unique_ptr<Compiled> c_owner(new (std::nothrow) Compiled());
     Compiled* c = c_owner.get();
     if (!c) return ABM_ENOMEM;
@@ -872,6 +881,7 @@ abm_status abm_batch_remove(abm_batch* b, int32_t sim) {
     const uint32_t zero = 0;
     CU(cudaMemcpyAsync(&b->B.sims[sim].active, &zero, 4, cudaMemcpyHostToDevice, b->stream));
     b->sims[sim].state = 2;
+    b->live_valid = false;
     b->model_refs[b->sims[sim].model_slot]--;
     return repack_cells(b);
 }
@@ -984,11 +994,17 @@ abm_status abm_batch_step(abm_batch* b, uint32_t n) {
     if (n > 0)
         for (auto& h : b->sims)
             if (h.state == 2) h.state = 0;  // their agents are dropped by this step
+    const uint32_t steps = n;
+    cudaGraphExec_t g1 = b->live_on ? b->g1_live : b->g1, g8 = b->live_on ? b->g8_live : b->g8;
     while (n >= 8) {
-        CU(cudaGraphLaunch(b->g8, b->stream));
+        CU(cudaGraphLaunch(g8, b->stream));
         n -= 8;
     }
-    while (n--) CU(cudaGraphLaunch(b->g1, b->stream));
+    while (n--) CU(cudaGraphLaunch(g1, b->stream));
+    if (steps) {
+        b->epoch_host += steps;
+        b->live_valid = b->live_on != 0;
+    }
     return ABM_OK;
 }
 
@@ -1003,7 +1019,7 @@ abm_status abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, ui
     double acc[kStepKernels] = {};
     cudaError_t e = cudaSuccess;
     for (uint32_t s = 0; s < n && e == cudaSuccess; s++) {
-        e = launch_step_timed(b->B, b->L, b->stream, ev);
+        e = launch_step_timed(b->B, b->L, b->stream, ev, b->live_on != 0);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[kStepKernels]);
         for (int k = 0; k < kStepKernels && e == cudaSuccess; k++) {
             float ms = 0;
@@ -1013,6 +1029,10 @@ abm_status abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, ui
     }
     for (int k = 0; k <= kStepKernels; k++) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return cuda_fail(b, e, "profile step");
+    if (n) {
+        b->epoch_host += n;
+        b->live_valid = b->live_on != 0;
+    }
     for (int k = 0; k < kStepKernels; k++) kernel_ms[k] = (float)acc[k];
     return sync_and_check(b);
 }
@@ -1057,16 +1077,38 @@ abm_status abm_batch_counts(abm_batch* b, int32_t sim, uint64_t* out, size_t cap
 
 abm_status abm_batch_counts_begin(abm_batch* b, int32_t sim, uint32_t slot) {
     if (!b || slot >= ABM_READ_SLOTS || b->rs[slot].pending) return ABM_EINVAL;
-    abm_status st = observe(b, sim, 0);
-    if (st != ABM_OK) return st;
+    if (b->failed) return ABM_ESTATE;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    // live counts of the last step's result when they hold the current state,
+    // else a pass over the agents
+    const uint64_t* src = b->B.live + (size_t)((b->epoch_host - 1u) & 1u) * b->B.live_stride;
+    if (!b->live_valid) {
+        abm_status st = observe(b, sim, 0);
+        if (st != ABM_OK) return st;
+        src = b->B.counts;
+    }
     auto& r = b->rs[slot];
     r.n = b->sims[sim].n_counts;
-    // stream order keeps a later read's reset of the counts behind this copy
-    CU(cudaMemcpyAsync(r.host, b->B.counts + (size_t)sim * 512, 8 * (size_t)r.n, cudaMemcpyDeviceToHost,
-                       b->stream));
+    // stream order keeps a later reset of these counts behind this copy
+    CU(cudaMemcpyAsync(r.host, src + (size_t)sim * 512, 8 * (size_t)r.n, cudaMemcpyDeviceToHost, b->stream));
     CU(cudaMemcpyAsync(r.host + 512, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     CU(cudaEventRecord(r.done, b->stream));
     r.pending = true;
+    return ABM_OK;
+}
+
+abm_status abm_batch_live_counts(abm_batch* b, int on) {
+    if (!b) return ABM_EINVAL;
+    if (b->failed) return ABM_ESTATE;
+    if (on && !b->g1_live) {  // the step graphs with the counting move pass
+        CU(cudaStreamSynchronize(b->stream));
+        abm_status st = capture(b, true);
+        if (st != ABM_OK) return st;
+    }
+    b->live_on = on ? 1u : 0u;
+    b->live_valid = false;  // from the next step on
+    CU(cudaMemsetAsync(b->B.live, 0, 2 * 8 * (size_t)b->B.live_stride, b->stream));
+    CU(cudaMemcpyAsync(&b->B.ctl->live_counts, &b->live_on, 4, cudaMemcpyHostToDevice, b->stream));
     return ABM_OK;
 }
 
@@ -1149,6 +1191,8 @@ void abm_batch_destroy(abm_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->g1) cudaGraphExecDestroy(b->g1);
     if (b->g8) cudaGraphExecDestroy(b->g8);
+    if (b->g1_live) cudaGraphExecDestroy(b->g1_live);
+    if (b->g8_live) cudaGraphExecDestroy(b->g8_live);
     if (b->own_arena && b->arena) cudaFree(b->arena);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -1294,6 +1338,7 @@ abm_status abm_counts_begin(abm_sim* s, uint32_t slot) {
 abm_status abm_counts_finish(abm_sim* s, uint32_t slot, uint64_t* out, size_t cap, size_t* n_out) {
     return s ? abm_batch_counts_finish(s->b, slot, out, cap, n_out) : ABM_EINVAL;
 }
+abm_status abm_live_counts(abm_sim* s, int on) { return s ? abm_batch_live_counts(s->b, on) : ABM_EINVAL; }
 abm_status abm_digest(abm_sim* s, uint64_t* out) { return s ? abm_batch_digest(s->b, s->id, out) : ABM_EINVAL; }
 abm_status abm_dump(abm_sim* s, abm_record* out, size_t cap, size_t* n_out) {
     return s ? abm_batch_dump(s->b, s->id, out, cap, n_out) : ABM_EINVAL;

@@ -16,7 +16,7 @@
 //                one counter per 128-byte line (kTileStride words apart) so
 //                that the atomics of different tiles meet in different L2 lines
 //   tsum[T+1]    exclusive tile prefixes (grids of more than kDirectTiles tiles)
-//   sims[S], models[S], obs (counts/digests), ctl
+//   sims[S], models[S], obs (counts/digests), live[2][S][512], ctl
 //
 // meta word: bits 0-5 species, 6-7 compartment, 8 carrier, 9 carrier is
 // reactant a, 10 dead, 11 absorbed (became hidden this step), 12-19 reaction
@@ -139,7 +139,7 @@ struct Ctl {
     uint32_t n_monitors;     // simulations with an active threshold monitor
     uint32_t blocks_done;    // blocks of k_accept finished this step
     uint32_t n_props;        // proposals of this step (list in props)
-    uint32_t pad;
+    uint32_t live_counts;    // 1: each step leaves the counts of its result in live[epoch & 1]
 };
 
 struct Buffers {
@@ -162,6 +162,7 @@ struct Buffers {
     SimDev* sims;
     ModelDev* models;
     uint64_t* counts;
+    uint64_t* live;          // [2][max sims][512]: counts of a step's result, by step parity
     uint64_t* digests;
     MonDev* mons;            // [max_sims]
     int32_t* mon_w;          // [max_sims][512] weights over the counts vector
@@ -175,7 +176,13 @@ struct Buffers {
     uint32_t cap_births;
     uint32_t n_tiles_max;
     uint32_t propose_chunk;  // sorted agents per proposal-search block round (multiple of 256)
+    uint32_t live_stride;    // entries of one live-counts buffer (max sims x 512)
 };
+
+// The live-counts buffer a step with this epoch fills.
+__device__ __forceinline__ uint64_t* live_buffer(const Buffers& B, uint32_t epoch) {
+    return B.live + (size_t)(epoch & 1u) * B.live_stride;
+}
 
 // ------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -289,14 +296,16 @@ struct Launch {
 int move_blocks_per_sm();
 
 cudaError_t prepare_kernels();
-cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s);
+// live: the move pass variant that also keeps live counts (ctl.live_counts on)
+cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool live = false);
 
 cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim,
                         uint32_t base, uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp);
 cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest);
 // The step with a CUDA event before and after each of its kernels (ev[0..6]).
 constexpr int kStepKernels = 6;
-cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev);
+cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev,
+                              bool live = false);
 // Between steps: drop the agents of retired simulations (counter: ctl.n_sorted).
 cudaError_t launch_compact(const Buffers& B, const Launch& L, cudaStream_t s);
 cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim, void* d_out,

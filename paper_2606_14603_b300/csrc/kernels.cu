@@ -191,6 +191,10 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, 
                     B.xpm[k] = q;
                     B.xid[k] = par;
                     B.xrk[k] = rank;  // the scatter finds the cell again from q
+                    if (ctl->live_counts)  // (rare: read here, not kept in registers)
+                        atomicAdd((unsigned long long*)&live_buffer(B, ctl->epoch)[S.counts_off +
+                                                                                   count_slot((uint32_t)q.w, Mo)],
+                                  1ull);
                 } else {
                     raise_error(ctl, ERR_CAPACITY_EXTRAS, k);
                 }
@@ -279,6 +283,7 @@ __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, 
 }
 
 
+template <bool kLive>
 __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
@@ -306,6 +311,21 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     const uint32_t w = bid * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint32_t len = ((n + warps - 1) / warps + 31u) & ~31u;
     const uint32_t wbeg = min(n, w * len), wend = min(n, wbeg + len);
+    // live counts of the step's result (the variant launched while they are
+    // on): the moved agents here.  A block's range is contiguous in cell
+    // order, so nearly all belong to the simulation of its first agent: a
+    // shared histogram for that one.
+    constexpr bool count_live = kLive;
+    __shared__ uint32_t s_live[kLive ? 512 : 1];
+    __shared__ uint32_t s_live_sim;
+    if (count_live) {
+        for (uint32_t k = threadIdx.x; k < 512; k += blockDim.x) s_live[k] = 0;
+        if (threadIdx.x == 0) {
+            const uint32_t first = min(n, bid * (blockDim.x >> 5) * len);
+            s_live_sim = first < n ? sim_of((uint32_t)pm[first].w) : kNone;
+        }
+        __syncthreads();
+    }
     int4 nx_p = make_int4(0, 0, 0, 0);
     uint32_t nx_id = 0;
     if (wbeg + lane < wend) {
@@ -342,14 +362,28 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
             if (tile != kNone && tile != t0) atomicAdd(&B.tcnt[tile * kTileStride], 1u);
         }
         if (i < wend) move_phase4(B, ctl, cur, i, a, rank);
+        if (count_live && (a.flags & 1u)) {
+            const uint32_t meta = (uint32_t)a.p.w, slot = count_slot(meta, *a.Mo);
+            if (sim_of(meta) == s_live_sim) atomicAdd(&s_live[slot], 1u);
+            else atomicAdd((unsigned long long*)&live_buffer(B, ctl->epoch)[a.S->counts_off + slot], 1ull);
+        }
     }
     if (run_n && lane == 0) atomicAdd(&B.tcnt[run_tile * kTileStride], run_n);
+    if (count_live) {
+        __syncthreads();
+        if (s_live_sim != kNone) {
+            uint64_t* L = live_buffer(B, ctl->epoch) + B.sims[s_live_sim].counts_off;
+            for (uint32_t k = threadIdx.x; k < 512; k += blockDim.x)
+                if (s_live[k]) atomicAdd((unsigned long long*)&L[k], (unsigned long long)s_live[k]);
+        }
+    }
 }
 
+template <bool kLive>
 __global__ void __launch_bounds__(kThreads, 4) k_move(Buffers B) {
     pdl_wait();
     if (ld_volatile(&B.ctl->err)) return;
-    move_pass(B, blockIdx.x, gridDim.x);
+    move_pass<kLive>(B, blockIdx.x, gridDim.x);
     pdl_trigger();
 }
 
@@ -513,6 +547,11 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
     // the scan has read this step's tile counts: zero them for the next step
     const uint32_t ntiles = (ctl->n_cells + kScanTile - 1) / kScanTile;
     for (uint32_t t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) B.tcnt[t * kTileStride] = 0;
+    if (ctl->live_counts) {  // the live counts the next step fills (the last step's were read by now)
+        uint64_t* L = live_buffer(B, ctl->epoch + 1u);
+        const uint32_t n_live = ctl->n_sims * 512u;
+        for (uint32_t k = bid * blockDim.x + threadIdx.x; k < n_live; k += nb * blockDim.x) L[k] = 0;
+    }
     const uint32_t stride = nb * blockDim.x;
     for (uint32_t j0 = bid * blockDim.x + threadIdx.x; j0 < total; j0 += kScatterILP * stride) {
         uint32_t rk[kScatterILP];
@@ -774,6 +813,12 @@ __device__ void finalize_block(Buffers& B) {
         if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
         B.pm[nxt][ns + k] = B.bpm[k];
         B.aid[nxt][ns + k] = (uint32_t)nid;
+        if (ctl->live_counts) {
+            const SimDev& S = B.sims[s];
+            atomicAdd((unsigned long long*)&live_buffer(B, ctl->epoch)[S.counts_off +
+                                                                       count_slot((uint32_t)B.bpm[k].w, B.models[S.model])],
+                      1ull);
+        }
     }
     __syncthreads();
     for (uint32_t q = 0; q < per; q++) {
@@ -786,6 +831,10 @@ __device__ void finalize_block(Buffers& B) {
     for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
         if (B.sims[s].active && B.sims[s].step < B.sims[s].max_step) B.sims[s].step += 1;
     __syncthreads();
+    if (ctl->live_counts)  // the last entry of a counts vector is the next id
+        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
+            if (B.sims[s].active)
+                live_buffer(B, ctl->epoch)[B.sims[s].counts_off + B.sims[s].n_counts - 1] = B.sims[s].next_id;
     if (threadIdx.x == 0) {
         ctl->n_in = ns + nb;
         ctl->n_extra = 0;
@@ -804,6 +853,7 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
     Ctl* ctl = B.ctl;
     const uint32_t nxt = ctl->cur ^ 1u;
     const uint32_t np = ctl->n_props;
+    uint64_t* live = ctl->live_counts ? live_buffer(B, ctl->epoch) : nullptr;
     int4* __restrict__ pm = B.pm[nxt];
     uint32_t* __restrict__ aid = B.aid[nxt];
     uint32_t* __restrict__ apar = B.apar[nxt];
@@ -818,6 +868,7 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
         const uint64_t ka = B.acc[i];
         uint32_t ma = *wa, mb = *wb;
         if ((uint32_t)kb != ida || ka != kEmpty) continue;
+        const uint32_t ma0 = ma, mb0 = mb;
         const SimDev& S = B.sims[sim_of(ma)];
         const ModelDev& Mo = B.models[S.model];
         const uint32_t r = Mo.rx_of[ma & M_SP][mb & M_SP];
@@ -836,6 +887,13 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
         }
         *wa = ma;
         *wb = mb;
+        if (live) {  // the move pass counted both as they were
+            unsigned long long* L = (unsigned long long*)live + S.counts_off;
+            atomicAdd(L + count_slot(ma0, Mo), ~0ull);
+            atomicAdd(L + count_slot(mb0, Mo), ~0ull);
+            if (!(ma & (M_DEAD | M_ABSORBED))) atomicAdd(L + count_slot(ma, Mo), 1ull);
+            if (!(mb & (M_DEAD | M_ABSORBED))) atomicAdd(L + count_slot(mb, Mo), 1ull);
+        }
     }
 }
 
@@ -1081,12 +1139,12 @@ cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B
 
 int move_blocks_per_sm() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move, kThreads, 0) != cudaSuccess || n < 1) n = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<false>, kThreads, 0) != cudaSuccess || n < 1) n = 4;
     return n;
 }
 
-cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s) {
-    cudaError_t e = launch_pdl(k_move, L.blocks_agents, s, B);
+cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool live) {
+    cudaError_t e = launch_pdl(live ? k_move<true> : k_move<false>, L.blocks_agents, s, B);
     if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_scatter, L.blocks_agents, s, B);
@@ -1095,9 +1153,10 @@ cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s) {
     return e;
 }
 
-cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev, bool live) {
     cudaEventRecord(ev[0], s);
-    k_move<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    if (live) k_move<true><<<L.blocks_agents, kThreads, 0, s>>>(B);
+    else k_move<false><<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[1], s);
     if (L.prefix_kernel) k_tile_prefix<<<1, 1024, 0, s>>>(B);
     cudaEventRecord(ev[2], s);

@@ -71,3 +71,80 @@ def test_slot_misuse_is_refused_and_the_handle_keeps_working(A):
     s.counts_begin(0)
     assert np.array_equal(s.counts_finish(0), s.counts())
     s.close()
+
+
+def _live_models():
+    import dataclasses
+    from test_oracle_p5 import _model
+    dense = _model()
+    dense = dataclasses.replace(
+        dense, species=[dataclasses.replace(sp, D=d) for sp, d in zip(dense.species, [2.0, 1.0, 1.5, 0.5])],
+        reactions=[dataclasses.replace(r, p_release=0.2) if r.kind == W.BIND else r for r in dense.reactions])
+    return {"toy": (W.toy(700, 600, edge_um=0.45), 3, 60),
+            "mapk": (W.mapk(30_000), 4, 40),
+            "nuclear": (W.nuclear(20_000, boost=100.0, n_genes=16, genes_on=8), 5, 40),
+            "dense": (dense, 6, 40)}
+
+
+@pytest.mark.parametrize("name", ["toy", "mapk", "nuclear", "dense"])
+def test_live_counts_equal_the_counting_pass_and_the_oracle(A, oracle_mod, name):
+    """With live counts on, the step itself keeps the counts of its result
+    (moves and P1 changes counted by the move pass, reactions and complexes
+    by the acceptance walk, births by the bookkeeping): equal, at every step,
+    to the pass over all agents and to the oracle.  Read pipelined, one step
+    in flight, then after an 8-step graph."""
+    m, seed, steps = _live_models()[name]
+    s = A.Sim(m, seed, births_per_step=4096)
+    s.live_counts(True)
+    o = oracle_mod.OracleSim(m, seed)
+    want = []
+    for k in range(steps):
+        s.step(1)
+        s.counts_begin(k % 2)
+        o.step(1)
+        want.append(o.counts())
+        if k:
+            assert np.array_equal(s.counts_finish((k - 1) % 2), want[k - 1]), (name, k)
+    assert np.array_equal(s.counts_finish((steps - 1) % 2), want[-1]), name
+    s.step(8)
+    o.step(8)
+    s.counts_begin(0)
+    live = s.counts_finish(0)
+    assert np.array_equal(live, s.counts()) and np.array_equal(live, o.counts()), name
+    o.close()
+    s.close()
+
+
+def test_live_counts_across_admissions_and_removals(A):
+    """A batch whose members change: a read right after an admission or a
+    removal counts the agents (the live counts lack the change until a step
+    has run), later reads use the live counts; all equal the counting pass."""
+    sims = [(W.mapk(9_000), 3), (W.toy(700, 600, edge_um=0.45), 4), (W.nuclear(8_000, boost=50.0, n_genes=8,
+                                                                             genes_on=4), 5)]
+    extra = (W.mapk(6_000, drug_frac=0.0), 6)
+    cap_a, cap_c = A.batch_capacity([m for m, _ in sims] + [extra[0]])
+    bt = A.Batch(cap_a, cap_c, 4, births_per_step=4096)
+    ids = [bt.add(m, s) for m, s in sims]
+    bt.live_counts(True)
+
+    def check(active):
+        for slot, sid in enumerate(active):
+            bt.counts_begin(sid, slot % A.READ_SLOTS)
+            got = bt.counts_finish(slot % A.READ_SLOTS)
+            assert np.array_equal(got, bt.counts(sid)), sid
+
+    bt.step(5)
+    check(ids)
+    ids.append(bt.add(*extra))   # read right away: falls back to the counting pass
+    check(ids)
+    bt.step(3)
+    check(ids)
+    bt.remove(ids[1])
+    active = [i for k, i in enumerate(ids) if k != 1]
+    check(active)
+    bt.step(4)
+    check(active)
+    bt.live_counts(False)
+    bt.step(2)
+    check(active)
+    bt.close()
