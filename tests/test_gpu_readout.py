@@ -148,3 +148,26 @@ def test_live_counts_across_admissions_and_removals(A):
     bt.step(2)
     check(active)
     bt.close()
+
+
+def test_live_counts_with_a_frozen_simulation(A):
+    """A simulation frozen at its last step (as the server freezes finished
+    jobs) keeps its agents in place: its live counts stay those of that step
+    while the batch steps on, equal to the counting pass."""
+    sims = [(W.mapk(9_000), 3), (W.nuclear(8_000, boost=50.0, n_genes=8, genes_on=4), 5)]
+    cap_a, cap_c = A.batch_capacity([m for m, _ in sims])
+    bt = A.Batch(cap_a, cap_c, 2, births_per_step=4096)
+    ids = [bt.add(m, s) for m, s in sims]
+    bt.live_counts(True)
+    bt.set_max_step(ids[0], 6)
+    frozen = None
+    for k in range(12):
+        bt.step(1)
+        for slot, sid in enumerate(ids):
+            bt.counts_begin(sid, slot)
+            got = bt.counts_finish(slot)
+            assert np.array_equal(got, bt.counts(sid)), (k, sid)
+            if sid == ids[0] and k >= 5:
+                frozen = got if frozen is None else frozen
+                assert np.array_equal(got, frozen), k
+    bt.close()
