@@ -224,6 +224,25 @@ def test_nuclear_full_size_prefix(A, oracle_mod):
     assert np.array_equal(g.counts(), o.counts())
 
 
+def test_nuclear_full_size_50_steps_against_the_oracle_record(A):
+    """The two-compartment workload at 4M agents for 50 steps, digest after
+    every step and counts every 10, against tests/golden/nuclear_4M_trace.txt,
+    which tests/golden/make_nuclear_4M.py writes from the oracle alone (about
+    20 s of oracle time per step)."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "nuclear_4M_trace.txt")) if not l.startswith("#")]
+    want = {int(r[0]): (int(r[1], 16), [int(v) for v in r[2:]]) for r in rows}
+    assert sorted(want) == list(range(51))
+    g = A.Sim(W.nuclear(4_000_000), W.NUCLEAR_SEED)
+    for t in range(51):
+        if t:
+            g.step(1)
+        d, counts = want[t]
+        assert g.digest() == d, f"step {t}"
+        if counts:
+            assert g.counts().tolist() == counts, f"step {t}"
+    g.close()
+
+
 def test_batch_members_equal_alone_and_oracle(A, oracle_mod):
     sims = [(W.mapk(8000 + 3000 * k, drug_frac=0.02 * k), 100 + k) for k in range(4)]
     sims.append((W.nuclear(12_000, boost=50.0, n_genes=16), 7))
