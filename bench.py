@@ -29,6 +29,7 @@ UNIT = "molecule-steps/s"
 # per-kernel bytes each launch must move per unit (agent or cell) in this
 # design; the step as a whole must read and rewrite the 20-byte agent record
 STEP_BYTES_PER_AGENT = 40
+E2E_STEPS = 500          # steps of the end-to-end loop (creation amortised over them)
 KERNEL_BYTES = {"k_move": (40, "agent"), "k_tile_prefix": (8 / 8192, "cell"), "k_scan": (12, "cell"),
                 "k_scatter": (53, "agent"), "k_propose": (24, "agent"), "k_accept": (4, "agent")}
 
@@ -192,17 +193,32 @@ def reduce_over_ranks(total_ms, molecule_steps, device="cuda"):
     return float(tmax[0]), float(t[1])
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo) and its core count."""
+    name = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return name, os.cpu_count() or 1
+
+
 def run_reference(args, rank):
-    """The oracle on the host cores, on a bounded sample of the same workload."""
+    """The oracle on the host cores, on a bounded sample of the same workload:
+    exactly `warmup` untimed steps, then `steps` timed steps (fewer only if
+    they would exceed the time budget, which the line then says)."""
     import oracle
     model, seed, name = workload(args)
     sim = oracle.OracleSim(model, seed)
     t0 = time.perf_counter()
     sim.step(1)
     est = time.perf_counter() - t0
+    if args.warmup > 1:
+        sim.step(args.warmup - 1)
     budget = args.ref_seconds
-    warm = min(args.warmup, max(0, int(0.1 * budget / max(est, 1e-6))))
-    sim.step(warm)
     steps = max(1, min(args.steps, int(budget / max(est, 1e-6))))
     n0 = molecules(sim.counts(), model)
     t0 = time.perf_counter()
@@ -210,12 +226,16 @@ def run_reference(args, rank):
     el = time.perf_counter() - t0
     n1 = molecules(sim.counts(), model)
     value = 0.5 * (n0 + n1) * steps / el
-    sample = f"{name}: {steps} oracle steps after {1 + warm} untimed, single thread"
+    cpu, cores = cpu_model()
+    sample = (f"{name}: {steps} oracle steps after {max(1, args.warmup)} untimed, single thread"
+              + ("" if steps == args.steps else f" (capped from {args.steps} by the {budget:.0f} s budget)"))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": steps, "warmup": 1 + warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": config_of(args, model, name),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "steps": steps, "warmup": max(1, args.warmup), "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": config_of(args, model, name, {"parallelism": f"replicas x{args.gpus}", "seed": seed}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu, "host_cores": cores},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -232,8 +252,10 @@ def cpu_baseline(model, seed, name, seconds=12.0):
         steps += 1
     el = time.perf_counter() - t0
     n = molecules(sim.counts(), model)
+    cpu, cores = cpu_model()
     return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{name}: the first {steps} steps from t = 0, serial oracle, one thread"}
+            "sample": f"{name}: the first {steps} steps from t = 0, serial oracle, one thread",
+            "cpu_model": cpu, "host_cores": cores}
 
 
 def _sweep_oracle_task(args):
@@ -262,7 +284,8 @@ def sweep_cpu_baseline(steps=2, scale=1.0):
         res = pool.map(_sweep_oracle_task, [(k, steps, scale) for k in range(n)], chunksize=1)
     ms = sum(r[0] for r in res)
     busy = sum(r[1] for r in res)
-    return {"value": ms / (busy / cores), "unit": UNIT, "cores": cores, "kind": "oracle",
+    cpu, _ = cpu_model()
+    return {"value": ms / (busy / cores), "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu,
             "sample": f"all {n} sweep simulations, the first {steps} steps of each from t = 0, serial "
                       f"oracle in {cores} worker processes; value = molecule-steps / (summed step "
                       f"seconds / {cores}), creation not timed"}
@@ -466,14 +489,18 @@ def main():
                  "achieved_gbs": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9,
                  "frac": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9 / hbm}
 
-    # end to end: create from host structs, K steps, every step's counts
-    # vector read back to the host: pipelined (the step keeps its result's
-    # counts; each step's copy is queued into a pinned slot and collected while
-    # the next step runs) and, for comparison, synchronous (abm_counts, a
-    # counting pass and a wait, after every step)
+    # end to end, through the C ABI with host-side inputs and outputs: the
+    # model structs go in by abm_create (upload and device-side placement,
+    # timed and reported on its own), then E2E_STEPS times (abm_step + that
+    # step's counts vector back to the host): pipelined (the step keeps its
+    # result's counts; each step's copy is queued into a pinned slot and
+    # collected while the next step runs) and, for comparison, synchronous
+    # (abm_counts, a counting pass and a wait, after every step).  `value`
+    # charges the creation to the loop (creation + steps); `steady_value`
+    # is the loop alone.  Fixed step count, independent of --steps.
     e2e = None
     if not args.no_e2e:
-        Ke = max(1, min(K, 500))
+        Ke = E2E_STEPS
 
         def e2e_run(pipelined):
             torch.cuda.synchronize()
@@ -481,6 +508,8 @@ def main():
             s2 = A.Sim(model, seed, stream=stream)
             if pipelined:
                 s2.live_counts(True)  # each step keeps its result's counts: a read is a copy
+            s2.sync()
+            t1 = time.perf_counter()
             cvec = None
             for k in range(Ke):
                 s2.step(1)
@@ -493,23 +522,25 @@ def main():
             if pipelined:
                 cvec = s2.counts_finish((Ke - 1) % 2)
             torch.cuda.synchronize()
-            el = time.perf_counter() - t0
+            t2 = time.perf_counter()
             s2.close()
-            return cvec, el
+            return cvec, t1 - t0, t2 - t1
 
-        cvec, el = e2e_run(True)
-        cvec_s, el_s = e2e_run(False)
+        cvec, cr, loop = e2e_run(True)
+        cvec_s, cr_s, loop_s = e2e_run(False)
         assert np.array_equal(cvec, cvec_s)
         n_counts = len(cvec)
         # host-to-device at creation: Gaussian table, integer model tables, sim entry, control words
         model_bytes = 2 * 65536 + 15376 + 512
-        e2e = {"value": molecules(cvec, model) * Ke / el, "unit": UNIT,
+        ms_e2e = molecules(cvec, model) * Ke
+        e2e = {"value": ms_e2e / (cr + loop), "unit": UNIT,
                "h2d_bytes_per_step": model_bytes / Ke, "d2h_bytes_per_step": 8 * n_counts,
-               "steps": Ke, "includes": "abm_create (model upload, device-side placement) + per step "
-                                       "abm_step + that step's counts read back to the host "
-                                       "(live counts, abm_counts_begin / abm_counts_finish, one step "
-                                       "in flight)",
-               "synchronous_value": molecules(cvec_s, model) * Ke / el_s}
+               "steps": Ke, "create_s": cr, "loop_s": loop, "steady_value": ms_e2e / loop,
+               "includes": f"abm_create (model upload, device-side placement; create_s) + {Ke} x "
+                           "(abm_step + that step's counts read back to the host: live counts, "
+                           "abm_counts_begin / abm_counts_finish, one step in flight); "
+                           "steady_value excludes the creation",
+               "synchronous_value": ms_e2e / (cr_s + loop_s), "synchronous_steady_value": ms_e2e / loop_s}
 
     sweep = None
     if args.sweep_steps > 0 and args.workload == "cascade" and not args.agents:

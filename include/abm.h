@@ -315,9 +315,16 @@ abm_status  abm_monitor_read(abm_sim* sim, abm_monitor_state* out, int64_t* trac
  *  - out == NULL: returns the record count in *n_out (a size query).
  *  - More than 131,072 records: ABM_ECAPACITY, with the limit named in
  *    abm_last_error; the handle stays usable (use abm_dump instead).
+ *  - cap below the record count: ABM_EINVAL (message in abm_last_error);
+ *    the handle stays usable.
+ *  - Call it with the device that was current when the handle was created
+ *    (the array is per device); with another device current it returns
+ *    ABM_EDEVICE and changes nothing.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.
+ *  - A failing CUDA call inside it returns ABM_ECUDA and leaves the handle
+ *    destroy-only, like any other call.
  *  - All calls share the array (each clears its counter first); calls that
  *    overlap on the GPU race.  Synchronous. */
 abm_status  abm_dump_noalloc(abm_sim* sim, abm_record* out, size_t cap, size_t* n_out);

@@ -284,6 +284,7 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
 
 // ------------------------------------------------------------------------
 struct abm_batch {
+    int device = 0;                      // CUDA device current at creation (owns arena and stream)
     uint64_t cap_agents = 0, cap_cells = 0;
     uint32_t max_sims = 0, cap_births = 0;
     cudaStream_t stream = nullptr;
@@ -599,6 +600,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     // launch shapes: grid-stride kernels sized to the resident capacity
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
+    b->device = dev;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t want = (b->cap_agents + 255) / 256;
     b->L.threads = 256;
@@ -1404,13 +1406,21 @@ abm_status abm_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* 
 // Internal view of a simulation handle for the library's other translation
 // units (no effect on any state).
 namespace abm {
-bool internal_view(abm_sim* s, Buffers* B, Launch* L, cudaStream_t* stream, int32_t* sim, std::string** err) {
+bool internal_view(abm_sim* s, Buffers* B, Launch* L, cudaStream_t* stream, int32_t* sim, std::string** err,
+                   int* device) {
     if (!s || !s->b || s->b->failed) return false;
     *B = s->b->B;
     *L = s->b->L;
     *stream = s->b->stream;
     *sim = s->id;
     *err = &s->b->err;
+    *device = s->b->device;
     return true;
+}
+
+// A CUDA failure seen by another translation unit: the handle becomes
+// destroy-only, exactly as after a failure inside this file.
+abm_status internal_cuda_fail(abm_sim* s, cudaError_t e, const char* where) {
+    return cuda_fail(s->b, e, where);
 }
 }  // namespace abm

@@ -23,7 +23,9 @@
 #include "engine.cuh"
 
 namespace abm {
-bool internal_view(abm_sim* s, Buffers* B, Launch* L, cudaStream_t* stream, int32_t* sim, std::string** err);
+bool internal_view(abm_sim* s, Buffers* B, Launch* L, cudaStream_t* stream, int32_t* sim, std::string** err,
+                   int* device);
+abm_status internal_cuda_fail(abm_sim* s, cudaError_t e, const char* where);
 }
 
 using namespace abm;
@@ -102,20 +104,25 @@ extern "C" abm_status abm_dump_noalloc(abm_sim* s, abm_record* out, size_t cap, 
     cudaStream_t stream;
     int32_t sim;
     std::string* err;
-    if (!internal_view(s, &B, &L, &stream, &sim, &err)) return ABM_ESTATE;
-    int dev = 0;
+    int owner = 0;
+    if (!internal_view(s, &B, &L, &stream, &sim, &err, &owner)) return ABM_ESTATE;
+    // the scratch array is per device: use the one of the device that holds
+    // the handle's agents, which must be the current one
+    int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        *err = "abm_dump_noalloc: no usable current device";
+    if (e != cudaSuccess || dev != owner || dev < 0 || dev >= kMaxDevices) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf,
+                      "abm_dump_noalloc: the handle lives on device %d but device %d is current", owner, dev);
+        *err = buf;
         return ABM_EDEVICE;
     }
     if (!g_scratch_addr[dev]) {  // set-up, once per device, with that device current
         void* addr = nullptr;
         e = cudaGetSymbolAddress(&addr, g_dump_scratch);
-        if (e != cudaSuccess || !addr) {
-            *err = std::string("abm_dump_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
-            return ABM_ECUDA;
-        }
+        if (e != cudaSuccess || !addr)
+            return internal_cuda_fail(s, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                                      "abm_dump_noalloc: cudaGetSymbolAddress");
         g_scratch_addr[dev] = addr;
     }
     DumpScratch* sc = static_cast<DumpScratch*>(g_scratch_addr[dev]);
@@ -127,10 +134,7 @@ extern "C" abm_status abm_dump_noalloc(abm_sim* s, abm_record* out, size_t cap, 
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&count, &sc->count, sizeof count, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) {
-        *err = std::string("abm_dump_noalloc: ") + cudaGetErrorString(e);
-        return ABM_ECUDA;
-    }
+    if (e != cudaSuccess) return internal_cuda_fail(s, e, "abm_dump_noalloc");
     *n_out = count;
     if (count > kNoAllocRecords) {
         char buf[192];
@@ -141,13 +145,15 @@ extern "C" abm_status abm_dump_noalloc(abm_sim* s, abm_record* out, size_t cap, 
         return ABM_ECAPACITY;
     }
     if (!out) return ABM_OK;  // size query
-    if (cap < count) return ABM_EINVAL;
+    if (cap < count) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "abm_dump_noalloc: output holds %zu records, %u needed", cap, count);
+        *err = buf;
+        return ABM_EINVAL;
+    }
     e = cudaMemcpyAsync(out, sc->rec, (size_t)count * sizeof(abm_record), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) {
-        *err = std::string("abm_dump_noalloc: ") + cudaGetErrorString(e);
-        return ABM_ECUDA;
-    }
+    if (e != cudaSuccess) return internal_cuda_fail(s, e, "abm_dump_noalloc: copy");
     std::sort(out, out + count, [](const abm_record& a, const abm_record& b) { return a.id < b.id; });
     return ABM_OK;
 }

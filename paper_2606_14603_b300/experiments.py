@@ -27,11 +27,12 @@ def volume_invariance(make_model: Callable[[int, float], object], doses: Sequenc
     """make_model(n_total, dose) builds the model at n_total agents (its
     volume in proportion); doses run at n_agents and at factor * n_agents.
     Returns the readout change (percent of the initial value) per dose and
-    volume, the largest difference between the volumes in percentage points,
-    and the wall time per step of each batch."""
+    volume, the readout itself every `period` steps (trace[volume][dose]),
+    the largest difference between the volumes in percentage points, and the
+    wall time per step of each batch."""
     period = period or max(1, steps // 20)
     out = {"doses": list(doses), "volumes": [1, factor], "steps": steps, "readout": list(readout),
-           "agents": [], "change_pct": [], "ms_per_step": [], "trace_period": period}
+           "agents": [], "change_pct": [], "ms_per_step": [], "trace_period": period, "trace": []}
     for vol in (1, factor):
         models = [make_model(n_agents * vol, d) for d in doses]
         cap_a, cap_c = batch_capacity(models)
@@ -45,14 +46,16 @@ def volume_invariance(make_model: Callable[[int, float], object], doses: Sequenc
             b.step(steps)
             b.sync()
             wall = time.perf_counter() - t0
-            change = []
+            change, traces = [], []
             for s in sids:
                 st = b.monitor_read(s)
                 first, last = int(st.trace[0]), int(st.trace[-1])
                 assert st.last_step == steps and len(st.trace) == steps // period + 1
                 change.append(100.0 * (last - first) / first)
+                traces.append([int(v) for v in st.trace])
             out["agents"].append(sum(m.n_agents for m in models))
             out["change_pct"].append(change)
+            out["trace"].append(traces)
             out["ms_per_step"].append(wall / steps * 1e3)
         finally:
             b.close()

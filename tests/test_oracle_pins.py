@@ -106,6 +106,50 @@ def test_gauss_step_second_moment_is_2Ddt(oracle_mod):
         assert abs(e2 - 2 * D * dt) / (2 * D * dt) < 2e-3
 
 
+def _exact_mult(D, dt, unit):
+    """2^20 * sqrt(2 D dt) * 1000 / unit as an exact value of the binary
+    inputs (rational arithmetic, the square root to 60 digits), returned with
+    its distance to the nearest rounding boundary (a half integer)."""
+    import decimal
+    from fractions import Fraction
+    decimal.getcontext().prec = 60
+    var = Fraction(D) * Fraction(dt) * 2                     # um^2, exact
+    root = decimal.Decimal(var.numerator).sqrt() / decimal.Decimal(var.denominator).sqrt()
+    scale = Fraction(1000) * Fraction(2 ** 20) / Fraction(unit)
+    v = root * decimal.Decimal(scale.numerator) / decimal.Decimal(scale.denominator)
+    frac = v - int(v)
+    return v, abs(frac - decimal.Decimal("0.5"))
+
+
+def test_mult_is_the_nearest_integer_of_its_definition(oracle_mod):
+    """M = round(2^20 * sigma / unit) with sigma = sqrt(2 D dt) (Sec. 2:
+    Brownian displacement from the diffusion coefficient; the fixed-point
+    reading of the step size).  Checked against exact arithmetic, not the
+    oracle's own floating-point order: over the workloads' coefficients and
+    2,000 random (D, dt, unit), M is the nearest integer of the exact value
+    (ties are not met: every case lies more than 1e-6 from a half integer),
+    halves are rounded away from zero, and a mistake such as a missing
+    factor 2, sigma^2 instead of sigma, or truncation instead of rounding
+    fails here."""
+    import decimal
+    rng = np.random.default_rng(20261204)
+    cases = [(D, 1e-6, 0.1) for D in (0.1, 1.0, 2.0, 3.0, 4.0, 10.0)]
+    cases += [(float(10 ** rng.uniform(-3, 2)), float(10 ** rng.uniform(-7, -4)),
+               float(rng.choice([0.05, 0.1, 0.25, 1.0]))) for _ in range(2000)]
+    truncations_differ = 0
+    for D, dt, unit in cases:
+        v, gap = _exact_mult(D, dt, unit)
+        assert gap > decimal.Decimal("1e-6"), (D, dt, unit)
+        want = int(v.to_integral_value(rounding=decimal.ROUND_HALF_UP))
+        got = oracle_mod.mult(D, dt, unit)
+        assert got == want, (D, dt, unit, got, str(v))
+        truncations_differ += int(v) != want
+    assert truncations_differ > 500          # the cases do tell rounding from truncation
+    # a worked value: D = 1 um^2/s, dt = 1 us, 0.1 nm units: sigma = 1.41421356 nm
+    # = 14.1421356 units; 2^20 * 14.1421356237... = 14,829,104.004 -> 14,829,104
+    assert oracle_mod.mult(1.0, 1e-6, 0.1) == 14_829_104
+
+
 # --------------------------------------------------------------------------
 def _exact_e2(oracle_mod, m):
     tab = oracle_mod.ncdf_table().astype(np.int64)

@@ -73,3 +73,18 @@ def test_noalloc_dump_rejects_more_than_its_array(A):
     sim.step(1)                                   # the handle is still usable
     assert len(sim.dump()) == 150_000
     sim.close()
+
+
+def test_noalloc_dump_refuses_a_short_output_and_keeps_the_handle(A):
+    sim = A.Sim(W.toy(400, 300, edge_um=0.4), 5)
+    sim.step(3)
+    f = _fn(A)
+    n = C.c_size_t()
+    assert f(sim._h, None, 0, C.byref(n)) == A.OK
+    short = np.zeros(n.value - 1, dtype=A.RECORD_DTYPE)
+    m = C.c_size_t()
+    assert f(sim._h, short.ctypes.data, short.size, C.byref(m)) == A.EINVAL
+    assert "needed" in A.lib().abm_last_error(sim._h).decode()
+    sim.step(2)                                   # not a failure of the handle
+    assert np.array_equal(_noalloc_dump(A, sim), sim.dump())
+    sim.close()

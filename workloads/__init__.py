@@ -267,3 +267,26 @@ def served_jobs(duration_s: float = 600.0, rate_per_s: float = 20.0, seed: int =
         model = mapk(n, drug_frac=0.05) if kind else nuclear(n, n_genes=max(1, n // 62_500))
         jobs.append(Job(len(jobs), t, model, job_seed, steps))
     return jobs
+
+
+# --------------------------------------------------------------------------
+# Birth-heavy model (expression, Sec. 2 and Sec. 3.4: expressors produce new
+# molecules at a fixed rate; degradation removes them).  n_emit expressors E
+# (p_emit per step, child C); C degrades with p 0.5 per step and itself
+# emits G with p 0.2; G degrades at its first step; bystanders X bind C
+# (BIND, released with p 0.2), so some parents are immune while bound.  At
+# p_emit = 1 a step sees about 1.4 * n_emit births.  Density about that of
+# the cascade (1,000 agents per um^3 at the start).
+def births(n_emit: int = 1000, p_emit: float = 1.0, n_bystanders: int | None = None,
+           edge_um: float | None = None) -> Model:
+    nx = n_emit if n_bystanders is None else n_bystanders
+    if edge_um is None:
+        edge_um = ((n_emit + nx) / 1000.0) ** (1.0 / 3.0)
+    sp = [
+        Species("E", n_emit, 0.5, p_emit=p_emit, emit=1),
+        Species("C", 0, 2.0, p_uni=0.5, uni_to=-1, p_emit=0.2, emit=2),
+        Species("G", 0, 3.0, p_uni=1.0, uni_to=-1),
+        Species("X", nx, 1.0),
+    ]
+    rx = [Reaction(3, 1, BIND, 3, 1, 30.0, 0.5, 0.2)]
+    return Model(name="births", species=sp, reactions=rx, compartments=[Compartment(CUBE, edge_um)])
