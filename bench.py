@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--sweep-steps", type=int, default=50, help="steps per sim in the sweep summary")
     p.add_argument("--serve-groups", type=int, default=4,
                    help="batches the server steps concurrently (one CUDA stream each)")
+    p.add_argument("--serve-rate", type=float, default=20.0, help="job arrivals per second (the served config: 20)")
+    p.add_argument("--serve-sub-rate", type=float, default=10.0,
+                   help="a rate below the GPU's capacity, served to completion (0 = skip)")
+    p.add_argument("--serve-admission", choices=["fifo", "backfill"], default="backfill")
     p.add_argument("--size-steps", type=int, default=100,
                    help="steps of the 4M/16M-agent cascade summary (0 = skip)")
     p.add_argument("--volume-steps", type=int, default=4000,
@@ -337,22 +341,25 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0, cpu=True):
             "serial_ms_per_round": serial_ms / steps}
 
 
-def run_serve(A, seconds, budget=150e9, groups=1):
-    """Served workload: Poisson arrivals (20/s, seed 7) of cascade or
+def run_serve(A, seconds, budget=150e9, groups=1, rate=20.0, drain=False, admission="backfill"):
+    """Served workload: Poisson arrivals (rate per s, seed 7) of cascade or
     two-compartment jobs, 10k-2M agents, 1k-20k steps, admitted under an HBM
-    budget, continuous batching; runs `seconds` of arrivals in real time and
-    reports the jobs that completed within that window."""
+    budget, continuous batching; `seconds` of arrivals in real time.  Without
+    drain the run stops at the end of the window and the jobs still queued or
+    running count in the latency at their age then (censored, lower bounds);
+    with drain every arrived job is served to completion."""
     import workloads as W
     from paper_2606_14603_b300 import serve
-    jobs = W.served_jobs(duration_s=seconds)
+    jobs = W.served_jobs(duration_s=seconds, rate_per_s=rate)
     srv = serve.Server(budget_bytes=budget, groups=groups)
-    out = serve.run(jobs, srv, duration_s=seconds, real_time=True, drain=False)
+    out = serve.run(jobs, srv, duration_s=seconds, real_time=True, drain=drain, admission=admission)
     srv.close()
     out.pop("results")
     out.pop("failed")
-    out["arrival_rate_per_s"] = 20.0
+    out["arrival_rate_per_s"] = rate
     out["budget_bytes"] = budget
     out["window_s"] = seconds
+    out["drained"] = drain
     out["groups"] = groups
     return out
 
@@ -381,12 +388,13 @@ def main():
 
     if args.workload == "serve":
         with Clocks(local) as clk:
-            sv = run_serve(A, args.serve_seconds, groups=args.serve_groups)
+            sv = run_serve(A, args.serve_seconds, groups=args.serve_groups, rate=args.serve_rate,
+                           admission=args.serve_admission)
         line = {"metric": METRIC, "value": sv["throughput_molecule_steps_per_s"], "unit": UNIT, "n_gpus": world,
                 "steps": sv["steps_run"], "warmup": 0, "ms_per_step": None, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": "served_poisson_20_per_s", "window_s": args.serve_seconds,
-                           "budget_gb": 150},
+                "config": {"workload": f"served_poisson_{args.serve_rate:g}_per_s", "window_s": args.serve_seconds,
+                           "budget_gb": 150, "admission": args.serve_admission},
                 "serve": sv, "clocks": clk.summary()}
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -546,10 +554,14 @@ def main():
     if args.sweep_steps > 0 and args.workload == "cascade" and not args.agents:
         sweep = run_sweep(A, torch, stream, args.sweep_steps, cpu=not args.no_cpu_baseline and world == 1)
 
-    served = None
+    served = served_sub = None
     if args.serve_seconds > 0 and args.workload == "cascade" and not args.agents:
         sim.close()
-        served = run_serve(A, args.serve_seconds, groups=args.serve_groups)
+        served = run_serve(A, args.serve_seconds, groups=args.serve_groups, rate=args.serve_rate,
+                           admission=args.serve_admission)
+        if args.serve_sub_rate > 0:
+            served_sub = run_serve(A, args.serve_seconds, groups=args.serve_groups, rate=args.serve_sub_rate,
+                                   drain=True, admission=args.serve_admission)
         sim = None
 
     sizes = None
@@ -607,7 +619,7 @@ def main():
             "roofline": roof, "step_roofline": step_roof,
             "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
             "gpu_launches": launches_per_step(sim_cells) * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
-            "serve": served, "sizes": sizes, "volume": volume,
+            "serve": served, "serve_subcapacity": served_sub, "sizes": sizes, "volume": volume,
             "clocks": clocks, "wall_s_timed_region": wall}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -114,7 +114,8 @@ typedef struct {
 typedef struct {
     uint64_t       capacity_agents;  /* 0 = initial count * 1.25 + 65536  */
     uint32_t       cell_log2;        /* grid cell = 2^k units; 0 = auto    */
-    uint32_t       births_per_step;  /* 0 = 8192 (also the maximum)        */
+    uint32_t       births_per_step;  /* births one step may add; 0 = 8192;
+                                        clamped to the agent capacity      */
     void*          arena;            /* device memory, or NULL = library   */
     size_t         arena_bytes;
     void*          stream;           /* cudaStream_t, or NULL = library    */
@@ -126,7 +127,10 @@ typedef struct {
     uint64_t       capacity_agents;  /* slots shared by all sims (> 0)     */
     uint64_t       capacity_cells;   /* grid cells shared by all sims      */
     uint32_t       max_sims;         /* 1..2048                            */
-    uint32_t       births_per_step;  /* 0 = 8192 (also the maximum)        */
+    uint32_t       births_per_step;  /* births one step may add to EACH
+                                        simulation (its segment of the births
+                                        buffer, 8 bytes per birth and slot);
+                                        0 = 8192; clamped to capacity_agents */
     void*          arena;
     size_t         arena_bytes;
     void*          stream;
@@ -219,6 +223,16 @@ abm_status  abm_batch_digest(abm_batch* b, int32_t sim_id, uint64_t* out);
 abm_status  abm_batch_dump(abm_batch* b, int32_t sim_id, abm_record* out, size_t cap,
                            size_t* n_out);
 abm_status  abm_batch_sync(abm_batch* b);
+/* Status of one simulation of the batch (synchronises).  A simulation whose
+ * births in one step exceed births_per_step stops there (Sec. 2 and
+ * Sec. 3.4: expression births): it is frozen at that step with a corrupt
+ * state, this call and its counts, digest, dump and monitor reads return
+ * ABM_ECAPACITY (message in abm_batch_last_error), and every other
+ * simulation of the batch goes on unaffected; the caller removes it.  For a
+ * handle of abm_create / abm_restore the same error fails the handle.
+ * Exceeding the batch's agent capacity still fails the whole batch.
+ * ABM_ESTATE for a free slot. */
+abm_status  abm_batch_sim_status(abm_batch* b, int32_t sim_id);
 /* Pipelined counts (the readout of Sec. 2, at every step if wanted, without
  * stalling the device): _begin queues the count pass for the state after the
  * steps issued so far and its copy into pinned host slot `slot` (0 ..

@@ -138,6 +138,7 @@ def lib():
             "abm_batch_digest": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
             "abm_batch_dump": (C.c_int, [P, C.c_int32, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "abm_batch_sync": (C.c_int, [P]),
+            "abm_batch_sim_status": (C.c_int, [P, C.c_int32]),
             "abm_batch_live_agents": (C.c_int, [P, C.POINTER(C.c_uint64)]),
             "abm_batch_last_error": (C.c_char_p, [P]),
             "abm_batch_destroy": (None, [P]),
@@ -449,6 +450,18 @@ class Batch:
         v = C.c_uint64()
         _check(lib().abm_batch_live_agents(self._h, C.byref(v)), lib().abm_batch_last_error, self._h)
         return v.value
+
+    def sim_status(self, sim: int) -> tuple:
+        """(status, message) of one simulation: (OK, "") or, for a simulation
+        stopped by its own error (births of one step beyond its limit), the
+        status and the library's message; the batch itself stays usable."""
+        st = lib().abm_batch_sim_status(self._h, sim)
+        if st == OK:
+            return OK, ""
+        msg = lib().abm_batch_last_error(self._h).decode()
+        if st == ESTATE and "simulation" not in msg:
+            raise AbmError(st, msg)
+        return st, msg
 
     def counts(self, sim: int) -> np.ndarray:
         out = np.zeros(self._n_counts[sim], dtype=np.uint64)

@@ -240,6 +240,15 @@ uint64_t cells_for(const Compiled& c, uint32_t shift) {
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// Births per step of one simulation (its segment of the births buffer):
+// the option, or kDefaultBirths, at most the agent capacity (a step adds at
+// most one child per agent), rounded up to even (16-byte segments).
+uint32_t births_quota(uint64_t want, uint64_t cap_agents) {
+    uint64_t q = want ? want : kDefaultBirths;
+    q = std::min<uint64_t>(q, std::max<uint64_t>(cap_agents, 1));
+    return (uint32_t)((q + 1) & ~1ull);
+}
+
 struct Layout {
     size_t off[32];
     size_t total;
@@ -255,7 +264,7 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
         4 * C, 4 * C, 4 * C, 4 * C,            // aid[2], apar[2]
         4 * C, 8 * C, 8 * C, (size_t)C,        // rk, acc, props, pflag
         16 * E, 4 * E, 4 * E,                  // extras
-        16 * (size_t)Bc, 4 * (size_t)Bc,       // births
+        8 * (size_t)Bc * S, 4 * ((size_t)S + 1),  // births: one segment per simulation slot, prefixes
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
         4 * kTileStride * tiles,               // tile counts (one per 128-byte line)
         4 * tiles,                             // tile prefixes
@@ -286,7 +295,8 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
 struct abm_batch {
     int device = 0;                      // CUDA device current at creation (owns arena and stream)
     uint64_t cap_agents = 0, cap_cells = 0;
-    uint32_t max_sims = 0, cap_births = 0;
+    uint32_t max_sims = 0, bquota = 0;
+    bool single = false;                 // created by abm_create / abm_restore: a simulation's error fails the handle
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     char* arena = nullptr;
@@ -301,6 +311,7 @@ struct abm_batch {
         uint64_t* host = nullptr;        // pinned: 512 counts, then a copy of the control block
         cudaEvent_t done = nullptr;
         uint32_t n = 0;
+        int32_t sim = -1;
         bool pending = false;
     };
     ReadSlot rs[ABM_READ_SLOTS];
@@ -309,8 +320,11 @@ struct abm_batch {
     bool live_valid = false;             // live counts hold the current state (a step ran with them on)
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;
     cudaGraphExec_t g1_live = nullptr, g8_live = nullptr;  // the same with live counts, captured on first use
+    uint32_t sim_errs_seen = 0;          // per-simulation errors already read from the device
     struct HostSim {
         int state = 0;  // 0 free, 1 active, 2 draining (removed, not yet stepped)
+        abm_status status = ABM_OK;     // a per-simulation error read from the device (sticky)
+        std::string err;
         uint32_t model_slot = 0;
         uint64_t n_cells = 0;
         uint32_t n_counts = 0;
@@ -381,9 +395,39 @@ abm_status check_device(std::string* msg) {
     return ABM_OK;
 }
 
+// Per-simulation errors (births of one step beyond a simulation's limit):
+// read the error words of the simulations when the device has counted new
+// ones; each failed simulation keeps its status, the batch goes on.  A
+// handle created as a single simulation fails as a whole.
+abm_status check_sim_errors(abm_batch* b, const Ctl& h) {
+    if (h.sim_errs == b->sim_errs_seen) return ABM_OK;
+    b->sim_errs_seen = h.sim_errs;
+    std::vector<SimDev> sd(b->n_sims_used);
+    if (!sd.empty()) {
+        cudaError_t e = cudaMemcpyAsync(sd.data(), b->B.sims, sizeof(SimDev) * sd.size(), cudaMemcpyDeviceToHost,
+                                        b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_fail(b, e, "reading simulation errors");
+    }
+    std::string first;
+    for (uint32_t s = 0; s < b->n_sims_used; s++) {
+        auto& hs = b->sims[s];
+        if (!sd[s].err || hs.status != ABM_OK || hs.state == 0) continue;
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "simulation %u: births of one step exceed its limit of %u (birth %u); the simulation "
+                      "is stopped, the other simulations go on", s, b->bquota, sd[s].err_info);
+        hs.status = ABM_ECAPACITY;
+        hs.err = buf;
+        if (first.empty()) first = buf;
+    }
+    if (b->single && !first.empty()) return fail(b, ABM_ECAPACITY, first);
+    return ABM_OK;
+}
+
 // Map the sticky device error word to a status.
 abm_status check_ctl(abm_batch* b, const Ctl& h) {
-    if (h.err == ERR_NONE) return ABM_OK;
+    if (h.err == ERR_NONE) return check_sim_errors(b, h);
     char buf[160];
     abm_status st = ABM_ECAPACITY;
     const char* what = "capacity exceeded";
@@ -406,6 +450,15 @@ abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
     const Ctl h = *b->h_ctl;
     if (out_ctl) *out_ctl = h;
     return check_ctl(b, h);
+}
+
+// The status of a simulation whose per-simulation error has been read
+// (ABM_OK otherwise); its message goes to the batch's last error.
+abm_status sim_status(abm_batch* b, int32_t sim) {
+    const auto& hs = b->sims[sim];
+    if (hs.status == ABM_OK) return ABM_OK;
+    b->err = hs.err;
+    return hs.status;
 }
 
 abm_status capture(abm_batch* b, bool live = false) {
@@ -463,21 +516,19 @@ uint64_t cells_in_use(const abm_batch* b) {
 
 // Drop the agents of retired simulations (between steps) and free their slots.
 abm_status compact(abm_batch* b, Ctl* h) {
-    const uint32_t zero = 0;
-    CU(cudaMemcpyAsync(&b->B.ctl->n_sorted, &zero, 4, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemsetAsync(&b->B.ctl->n_compact, 0, 4, b->stream));
     CU(launch_compact(b->B, b->L, b->stream));
     uint32_t kept = 0;
-    CU(cudaMemcpyAsync(&kept, &b->B.ctl->n_sorted, 4, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaMemcpyAsync(&kept, &b->B.ctl->n_compact, 4, cudaMemcpyDeviceToHost, b->stream));
     CU(cudaStreamSynchronize(b->stream));
     const uint32_t nxt = h->cur ^ 1u;
     CU(cudaMemcpyAsync(&b->B.ctl->cur, &nxt, 4, cudaMemcpyHostToDevice, b->stream));
-    CU(cudaMemcpyAsync(&b->B.ctl->n_in, &kept, 4, cudaMemcpyHostToDevice, b->stream));
-    CU(cudaMemsetAsync(&b->B.ctl->n_sorted, 0, 4, b->stream));
+    CU(cudaMemcpyAsync(&b->B.ctl->n_buf[nxt], &kept, 4, cudaMemcpyHostToDevice, b->stream));
     CU(cudaStreamSynchronize(b->stream));
     for (auto& s : b->sims)
         if (s.state == 2) s.state = 0;
     h->cur = nxt;
-    h->n_in = kept;
+    h->n_buf[nxt] = kept;
     return ABM_OK;
 }
 
@@ -495,7 +546,7 @@ void abm_ncdf_table(int16_t* out) {
 size_t abm_batch_arena_bytes(const abm_batch_options* o) {
     if (!o || !o->capacity_agents || !o->capacity_cells || !o->max_sims || o->max_sims > (uint32_t)kMaxSims)
         return 0;
-    const uint32_t births = o->births_per_step ? o->births_per_step : kMaxBirths;
+    const uint32_t births = births_quota(o->births_per_step, o->capacity_agents);
     return layout_for(o->capacity_agents, o->capacity_cells, o->max_sims, births).total;
 }
 
@@ -506,8 +557,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
         return ABM_EINVAL;
     if (o->capacity_agents >= 0x7FFFFFFFull || o->capacity_cells >= 0xFFFFF000ull) return ABM_EINVAL;
     if (o->blocks_per_sm > 64) return ABM_EINVAL;
-    const uint32_t births = o->births_per_step ? o->births_per_step : kMaxBirths;
-    if (births > kMaxBirths) return ABM_EINVAL;
+    const uint32_t births = births_quota(o->births_per_step, o->capacity_agents);
     std::string msg;
     abm_status st = check_device(&msg);
     if (st != ABM_OK) return st;
@@ -516,7 +566,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     b->cap_agents = o->capacity_agents;
     b->cap_cells = o->capacity_cells;
     b->max_sims = o->max_sims;
-    b->cap_births = births;
+    b->bquota = births;
     const Layout lay = layout_for(b->cap_agents, b->cap_cells, b->max_sims, births);
     auto destroy_and = [&](abm_status s) {
         abm_batch_destroy(b);
@@ -569,8 +619,8 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.xpm = (int4*)at();
     B.xid = (uint32_t*)at();
     B.xrk = (uint32_t*)at();
-    B.bpm = (int4*)at();
-    B.bpar = (uint32_t*)at();
+    B.bseg = (uint2*)at();
+    B.bofs = (uint32_t*)at();
     B.cnt = (uint32_t*)at();
     B.start = (uint32_t*)at();
     B.tcnt = (uint32_t*)at();
@@ -592,7 +642,8 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.cap_agents = b->cap_agents;
     B.cap_extras = b->cap_agents / 2 + 1;
     B.cap_cells = b->cap_cells;
-    B.cap_births = births;
+    B.bquota = births;
+    B.max_sims = b->max_sims;
     B.n_tiles_max = (uint32_t)((b->cap_cells + kTile - 1) / kTile);
     b->sims.resize(b->max_sims);
     b->cell_off_host.assign(b->max_sims, 0);
@@ -782,14 +833,14 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     int32_t slot = free_slot();
     bool draining = false;
     for (uint32_t s = 0; s < b->max_sims; s++) draining |= b->sims[s].state == 2;
-    if (draining && (slot < 0 || (uint64_t)h.n_in + c->n0 > b->cap_agents)) {
+    if (draining && (slot < 0 || (uint64_t)h.n_buf[h.cur] + c->n0 > b->cap_agents)) {
         st = compact(b, &h);
         if (st != ABM_OK) {
             return st;
         }
         slot = free_slot();
     }
-    if (slot < 0 || cells_in_use(b) + ncell > b->cap_cells || (uint64_t)h.n_in + c->n0 > b->cap_agents) {
+    if (slot < 0 || cells_in_use(b) + ncell > b->cap_cells || (uint64_t)h.n_buf[h.cur] + c->n0 > b->cap_agents) {
         b->err = slot < 0 ? "no free simulation slot"
                  : cells_in_use(b) + ncell > b->cap_cells ? "grid cells exhausted" : "agent capacity exhausted";
         return ABM_ECAPACITY;
@@ -830,6 +881,8 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     sd.max_step = 0xFFFFFFFFu;
     auto& hs = b->sims[slot];
     hs.state = 1;
+    hs.status = ABM_OK;
+    hs.err.clear();
     hs.model_slot = (uint32_t)mslot;
     hs.n_cells = ncell;
     hs.n_counts = c->dev.n_counts;
@@ -843,15 +896,19 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
         for (auto& p : rs.pm) p.w |= (int)((uint32_t)slot << M_SIM_SHIFT);
         const size_t k = rs.pm.size();
         if (k) {
-            CU(cudaMemcpyAsync(b->B.pm[h.cur] + h.n_in, rs.pm.data(), 16 * k, cudaMemcpyHostToDevice, b->stream));
-            CU(cudaMemcpyAsync(b->B.aid[h.cur] + h.n_in, rs.id.data(), 4 * k, cudaMemcpyHostToDevice, b->stream));
-            CU(cudaMemcpyAsync(b->B.apar[h.cur] + h.n_in, rs.par.data(), 4 * k, cudaMemcpyHostToDevice, b->stream));
+            CU(cudaMemcpyAsync(b->B.pm[h.cur] + h.n_buf[h.cur], rs.pm.data(), 16 * k, cudaMemcpyHostToDevice,
+                               b->stream));
+            CU(cudaMemcpyAsync(b->B.aid[h.cur] + h.n_buf[h.cur], rs.id.data(), 4 * k, cudaMemcpyHostToDevice,
+                               b->stream));
+            CU(cudaMemcpyAsync(b->B.apar[h.cur] + h.n_buf[h.cur], rs.par.data(), 4 * k, cudaMemcpyHostToDevice,
+                               b->stream));
         }
     } else {
-        CU(launch_init(b->B, b->L, b->stream, (uint32_t)slot, h.n_in, (uint32_t)c->n0, b->staging, c->dev.n_sp));
+        CU(launch_init(b->B, b->L, b->stream, (uint32_t)slot, h.n_buf[h.cur], (uint32_t)c->n0, b->staging,
+                       c->dev.n_sp));
     }
-    const uint32_t n_in = h.n_in + (uint32_t)c->n0;
-    CU(cudaMemcpyAsync(&b->B.ctl->n_in, &n_in, 4, cudaMemcpyHostToDevice, b->stream));
+    const uint32_t n_in = h.n_buf[h.cur] + (uint32_t)c->n0;
+    CU(cudaMemcpyAsync(&b->B.ctl->n_buf[h.cur], &n_in, 4, cudaMemcpyHostToDevice, b->stream));
     st = repack_cells(b);  // synchronises (host temporaries above stay alive until then)
     if (st != ABM_OK) return st;
     st = sync_and_check(b);
@@ -962,6 +1019,7 @@ abm_status abm_batch_monitor_read(abm_batch* b, int32_t sim, abm_monitor_state* 
     CU(cudaMemcpyAsync(ring.data(), b->B.mon_trace + (size_t)sim * kMonTrace, 8 * kMonTrace,
                        cudaMemcpyDeviceToHost, b->stream));
     abm_status st = sync_and_check(b);
+    if (st == ABM_OK) st = sim_status(b, sim);
     if (st != ABM_OK) return st;
     out->value = M.value;
     out->last_step = M.last_step;
@@ -1044,11 +1102,19 @@ abm_status abm_batch_sync(abm_batch* b) {
     return sync_and_check(b);
 }
 
+abm_status abm_batch_sim_status(abm_batch* b, int32_t sim) {
+    if (!b) return ABM_EINVAL;
+    abm_status st = sync_and_check(b);
+    if (st != ABM_OK) return st;
+    if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
+    return sim_status(b, sim);
+}
+
 abm_status abm_batch_live_agents(abm_batch* b, uint64_t* out) {
     if (!b || !out) return ABM_EINVAL;
     Ctl h;
     abm_status st = sync_and_check(b, &h);
-    if (st == ABM_OK) *out = h.n_in;
+    if (st == ABM_OK) *out = h.n_buf[h.cur];
     return st;
 }
 
@@ -1072,6 +1138,7 @@ abm_status abm_batch_counts(abm_batch* b, int32_t sim, uint64_t* out, size_t cap
     if (out && cap) CU(cudaMemcpyAsync(b->h_counts, b->B.counts + (size_t)sim * 512, 8 * std::min(cap, n),
                                        cudaMemcpyDeviceToHost, b->stream));
     st = sync_and_check(b);
+    if (st == ABM_OK) st = sim_status(b, sim);
     if (st == ABM_OK && out && cap) std::memcpy(out, b->h_counts, 8 * std::min(cap, n));
     if (st == ABM_OK && out && cap < n) return ABM_EINVAL;
     return st;
@@ -1091,6 +1158,7 @@ abm_status abm_batch_counts_begin(abm_batch* b, int32_t sim, uint32_t slot) {
     }
     auto& r = b->rs[slot];
     r.n = b->sims[sim].n_counts;
+    r.sim = sim;
     // stream order keeps a later reset of these counts behind this copy
     CU(cudaMemcpyAsync(r.host, src + (size_t)sim * 512, 8 * (size_t)r.n, cudaMemcpyDeviceToHost, b->stream));
     CU(cudaMemcpyAsync(r.host + 512, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
@@ -1123,6 +1191,7 @@ abm_status abm_batch_counts_finish(abm_batch* b, uint32_t slot, uint64_t* out, s
     Ctl h;
     std::memcpy(&h, r.host + 512, sizeof(Ctl));
     abm_status st = check_ctl(b, h);
+    if (st == ABM_OK && r.sim >= 0 && (uint32_t)r.sim < b->max_sims) st = sim_status(b, r.sim);
     if (st != ABM_OK) return st;
     if (n_out) *n_out = r.n;
     if (out && cap) std::memcpy(out, r.host, 8 * std::min<size_t>(cap, r.n));
@@ -1135,6 +1204,7 @@ abm_status abm_batch_digest(abm_batch* b, int32_t sim, uint64_t* out) {
     if (st != ABM_OK) return st;
     CU(cudaMemcpyAsync(b->h_counts, b->B.digests + sim, 8, cudaMemcpyDeviceToHost, b->stream));
     st = sync_and_check(b);
+    if (st == ABM_OK) st = sim_status(b, sim);
     if (st == ABM_OK) *out = b->h_counts[0];
     return st;
 }
@@ -1145,8 +1215,9 @@ abm_status abm_batch_dump(abm_batch* b, int32_t sim, abm_record* out, size_t cap
     if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
     Ctl h;
     abm_status st = sync_and_check(b, &h);
+    if (st == ABM_OK) st = sim_status(b, sim);
     if (st != ABM_OK) return st;
-    const uint32_t dcap = (uint32_t)std::min<uint64_t>(2ull * h.n_in + 1, 0xFFFFFFF0ull);
+    const uint32_t dcap = (uint32_t)std::min<uint64_t>(2ull * h.n_buf[h.cur] + 1, 0xFFFFFFF0ull);
     void* d = nullptr;
     CU(cudaMalloc(&d, (size_t)dcap * 24));
     const uint32_t zero = 0;
@@ -1271,6 +1342,7 @@ abm_status abm_create(const abm_model* model, uint64_t seed, const abm_options* 
     abm_batch* b = nullptr;
     st = abm_batch_create(&o, &b);
     if (st != ABM_OK) return st;
+    b->single = true;
     int32_t id = -1;
     st = abm_batch_add(b, model, seed, shift, &id);
     if (st != ABM_OK) {
@@ -1313,6 +1385,7 @@ abm_status abm_restore(const abm_model* model, uint64_t seed, const abm_options*
     abm_batch* b = nullptr;
     st = abm_batch_create(&o, &b);
     if (st != ABM_OK) return st;
+    b->single = true;
     int32_t id = -1;
     st = abm_batch_restore(b, model, seed, shift, records, n_records, step, next_id, &id);
     if (st != ABM_OK) {

@@ -10,13 +10,21 @@
 //   props[C]     (proposer, target) sorted indices of this step's proposals
 //   pflag[C]     1 if the sorted agent is a free proposer (written by the scatter)
 //   xpm/xid/xrk  released partners appended by the move pass (C/2 + 1)
-//   bpm/bpar     births of the step (B)
+//   bseg[S][Q]   births of the step, one segment of Q per simulation slot:
+//                (parent's slot in the moved buffer, parent id)
+//   bofs[S+1]    births placed before each simulation this step (prefix)
 //   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
 //   tcnt[T]      agents per cell tile (8192 cells), counted by the move pass,
 //                one counter per 128-byte line (kTileStride words apart) so
 //                that the atomics of different tiles meet in different L2 lines
 //   tsum[T+1]    exclusive tile prefixes (grids of more than kDirectTiles tiles)
 //   sims[S], models[S], obs (counts/digests), live[2][S][512], ctl
+//
+// Step-local counters (released partners, proposals, births) are indexed by
+// the parity of the global step counter `epoch`: a step with epoch E uses
+// parity E & 1, and the bookkeeping block of k_scan (which advances epoch
+// to E + 1) clears the counters of the other parity for the next step, so
+// no kernel ever resets a counter another kernel of the same step reads.
 //
 // meta word: bits 0-5 species, 6-7 compartment, 8 carrier, 9 carrier is
 // reactant a, 10 dead, 11 absorbed (became hidden this step), 12-19 reaction
@@ -32,7 +40,7 @@ constexpr int kMaxSpecies = 64;
 constexpr int kMaxReactions = 255;
 constexpr int kMaxComp = 4;
 constexpr int kMaxSims = 2048;
-constexpr uint32_t kMaxBirths = 8192;
+constexpr uint32_t kDefaultBirths = 8192;   // default births per step of one simulation
 constexpr int kScanTile = 8192;           // cells per scan tile (256 threads x 32)
 constexpr int kTileStride = 32;           // words between two tile counters
 constexpr uint32_t kDirectTiles = 8192;   // up to this many tiles, each scan block adds up its own prefix
@@ -59,6 +67,10 @@ enum : uint32_t {
     ERR_PLACEMENT = 5,
     ERR_ID_SPACE = 6,
     ERR_CAPACITY_DUMP = 7,
+};
+// per-simulation error codes (SimDev.err): the simulation stops, the batch goes on
+enum : uint32_t {
+    SIM_ERR_BIRTHS = 1,      // births of one step beyond the simulation's limit
 };
 
 struct SpeciesDev {          // 48 bytes
@@ -105,7 +117,14 @@ struct SimDev {              // per simulation slot
     uint32_t n_counts;       // counts vector length
     uint32_t counts_off;     // offset into the counts buffer
     uint32_t max_step;       // the sim is frozen (kept, not advanced) once step reaches this
-    uint32_t pad[2];
+    // step-local words (written on the device each step)
+    uint32_t tau;            // step index of the step in flight (read by the proposal search)
+    uint32_t adv;            // 1: the step in flight advances this simulation
+    uint32_t nbc[2];         // births reserved by the move pass, by step parity
+    uint32_t nb;             // births placed by the step in flight
+    uint32_t nid0;           // id of the step's first child (next_id before the step's births)
+    uint32_t err;            // per-simulation error (SIM_ERR_*), sticky; the simulation is frozen
+    uint32_t err_info;
 };
 
 // Threshold monitor of one simulation slot (Sec. 2: designated species
@@ -124,22 +143,23 @@ struct MonDev {
 };
 
 struct Ctl {
-    uint32_t n_in;           // agents in the current buffer
-    uint32_t n_extra;        // released partners of this step
-    uint32_t n_sorted;       // agents after the scatter
-    uint32_t n_births;       // births of this step
-    uint32_t cur;            // current buffer
+    uint32_t n_buf[2];       // agents in buffer 0 / 1
+    uint32_t cur;            // buffer holding the state between steps (flipped by k_scan's bookkeeping)
+    uint32_t n_sorted;       // agents placed by this step's scatter
     uint32_t n_cells;        // cells in use
-    uint32_t pad0;
-    uint32_t epoch;          // global step counter
+    uint32_t epoch;          // global step counter (1 + steps run)
     uint32_t err;
     uint32_t err_info;
     uint32_t n_sims;         // sim slots in use (upper bound of the table)
     uint32_t dump_n;
     uint32_t n_monitors;     // simulations with an active threshold monitor
-    uint32_t blocks_done;    // blocks of k_accept finished this step
-    uint32_t n_props;        // proposals of this step (list in props)
+    uint32_t n_extra[2];     // released partners, by step parity
+    uint32_t n_props[2];     // proposals (list in props), by step parity
+    uint32_t nb_total;       // births placed by the step in flight
     uint32_t live_counts;    // 1: each step leaves the counts of its result in live[epoch & 1]
+    uint32_t n_compact;      // agents kept by a compaction (between steps)
+    uint32_t sim_errs;       // simulations that raised a per-simulation error
+    uint32_t pad[3];
 };
 
 struct Buffers {
@@ -153,8 +173,8 @@ struct Buffers {
     int4* xpm;
     uint32_t* xid;
     uint32_t* xrk;
-    int4* bpm;
-    uint32_t* bpar;
+    uint2* bseg;             // [max sims][bquota] births: (parent slot, parent id)
+    uint32_t* bofs;          // [max sims + 1] births before each simulation this step
     uint32_t* cnt;
     uint32_t* start;
     uint32_t* tcnt;
@@ -173,10 +193,11 @@ struct Buffers {
     uint64_t cap_agents;
     uint64_t cap_extras;
     uint64_t cap_cells;
-    uint32_t cap_births;
+    uint32_t bquota;         // births per step of one simulation (segment length)
     uint32_t n_tiles_max;
     uint32_t propose_chunk;  // sorted agents per proposal-search block round (multiple of 256)
     uint32_t live_stride;    // entries of one live-counts buffer (max sims x 512)
+    uint32_t max_sims;       // simulation slots
 };
 
 // The live-counts buffer a step with this epoch fills.
@@ -294,6 +315,7 @@ struct Launch {
 
 // CTAs of k_move that fit on one SM at once (its registers decide).
 int move_blocks_per_sm();
+size_t propose_smem(const Buffers& B);
 
 cudaError_t prepare_kernels();
 // live: the move pass variant that also keeps live counts (ctl.live_counts on)

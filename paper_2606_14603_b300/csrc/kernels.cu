@@ -7,15 +7,18 @@
 // CUDA graph replays them unchanged:
 //
 //   k_move      P1 events + P2 Brownian move + cell key + histogram rank
-//               (and agents per tile of 8192 cells)
+//               (and agents per tile of 8192 cells); births are reserved in
+//               their simulation's segment
 //   k_tile_prefix  prefixes of the per-tile agent counts (grids of more
 //               than 8192 tiles only)
-//   k_scan      exclusive scan of the cell histogram, tile prefixes included
+//   k_scan      exclusive scan of the cell histogram, tile prefixes included;
+//               one extra block does the step's bookkeeping meanwhile (births
+//               per simulation, monitors, step counters, buffer flip)
 //   k_scatter   reorder every live agent by cell into the other buffer
 //   k_propose   neighbour query over the cells a contact radius can reach,
-//               nearest eligible partner, atomicMin on a packed key
-//   k_accept    final-edge rule and reaction application; its last block
-//               runs the births (ids ranked by parent id) and bookkeeping
+//               nearest eligible partner, atomicMin on a packed key; births
+//               ranked by parent id and placed after the sorted agents
+//   k_accept    final-edge rule and reaction application
 //
 // The engine never depends on storage order: every decision is a function
 // of the set of (id, state) pairs, so atomics may run in any order.
@@ -155,7 +158,8 @@ __device__ __forceinline__ void monitor_eval(Buffers& B, uint32_t s) {
 
 // Phase 1: P1 events (a released partner is moved and placed right away:
 // rare) and the move draw; issues the three table loads.
-__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, MoveState& a) {
+__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t par, uint32_t i,
+                                            MoveState& a) {
     uint32_t meta = (uint32_t)a.p.w;
     a.flags = 0;
     if (meta & (M_DEAD | M_ABSORBED)) return;
@@ -165,7 +169,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, 
     a.S = &S;
     a.Mo = &Mo;
     const uint32_t t = S.step;
-    if (t >= S.max_step) {  // frozen: kept in place, not advanced
+    if (t >= S.max_step || S.err) {  // frozen (or failed): kept in place, not advanced
         a.flags = 1u;
         return;
     }
@@ -183,7 +187,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, 
                 int4 q = a.p;
                 q.w = (int)with_species(meta, (uint32_t)hprod, Mo);
                 brownian_move(S, Mo.sp[hprod], B.ztab, q, par, t);
-                const uint32_t k = reserve(&ctl->n_extra);
+                const uint32_t k = reserve(&ctl->n_extra[par]);
                 if (k < B.cap_extras) {
                     const uint32_t key = cell_of(S, q.x, q.y, q.z);
                     const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
@@ -259,27 +263,35 @@ __device__ __forceinline__ void move_phase2(MoveState& a) {
     a.key = cell_of(S, a.p.x, a.p.y, a.p.z);
 }
 
+// A birth of this step in its simulation's segment of the births buffer:
+// (the parent's slot in the moved buffer, its id).  The lanes of one
+// simulation reserve together; beyond the simulation's limit its own error
+// word is set (the simulation stops, the others go on).
+__device__ __noinline__ void reserve_birth(Buffers& B, Ctl* ctl, uint32_t par, uint32_t sim, uint32_t slot,
+                                              uint32_t id) {
+    cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), (int)sim);
+    SimDev& S = B.sims[sim];
+    uint32_t base = 0;
+    if (grp.thread_rank() == 0) base = atomicAdd(&S.nbc[par], grp.size());
+    const uint32_t k = grp.shfl(base, 0) + grp.thread_rank();
+    if (k < B.bquota) {
+        B.bseg[(size_t)sim * B.bquota + k] = make_uint2(slot, id);
+    } else if (atomicCAS(&S.err, 0u, SIM_ERR_BIRTHS) == 0u) {
+        S.err_info = k;
+        atomicAdd(&ctl->sim_errs, 1u);
+    }
+}
+
 // Phase 4: results (the histogram rank comes from the atomic between) and births.
-__device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, const MoveState& a,
-                                            uint32_t rank) {
+__device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t par, uint32_t i,
+                                            const MoveState& a, uint32_t rank) {
     if (!(a.flags & 1u)) {
         B.rk[i] = kNone;
         return;
     }
     B.rk[i] = rank;  // the scatter finds the cell again from the moved record
     B.pm[cur][i] = a.p;
-    if (a.flags & 2u) {
-        const uint32_t meta = (uint32_t)a.p.w;
-        const uint32_t k = reserve(&ctl->n_births);
-        if (k < B.cap_births) {
-            const uint32_t child = (uint32_t)a.Mo->sp[meta & M_SP].emit;
-            B.bpm[k] = make_int4(a.p.x, a.p.y, a.p.z,
-                                 (int)with_species(meta & ~(M_RXN | M_BOUND | M_ROLE_A), child, *a.Mo));
-            B.bpar[k] = a.id;
-        } else {
-            raise_error(ctl, ERR_CAPACITY_BIRTHS, k);
-        }
-    }
+    if (a.flags & 2u) reserve_birth(B, ctl, par, sim_of((uint32_t)a.p.w), i, a.id);
 }
 
 
@@ -287,12 +299,12 @@ template <bool kLive>
 __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
-    const uint32_t n = ctl->n_in;
-    if (bid == 0 && threadIdx.x == 0) ctl->n_sorted = 0;  // the scan writes the real count
+    const uint32_t n = ctl->n_buf[cur];
+    const uint32_t epoch = ctl->epoch, par = epoch & 1u;
     const int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
     // proposal slots touched last step become empty again (the list is short)
-    const uint32_t np = ctl->n_props;
+    const uint32_t np = ctl->n_props[par ^ 1u];
     const uint32_t stride = nb * blockDim.x;
     for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
     // threshold monitors add up the records as they stand after t steps (a
@@ -344,7 +356,7 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
             nx_id = aid[i + 32];
         }
         if (i < wend) {
-            move_phase1(B, ctl, cur, i, a);
+            move_phase1(B, ctl, cur, par, i, a);
             move_phase2(a);
         }
         const uint32_t rank = (a.flags & 1u) ? atomicAdd(&B.cnt[a.key], 1u) : 0u;
@@ -361,18 +373,18 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
             run_n += __popc(same);
             if (tile != kNone && tile != t0) atomicAdd(&B.tcnt[tile * kTileStride], 1u);
         }
-        if (i < wend) move_phase4(B, ctl, cur, i, a, rank);
+        if (i < wend) move_phase4(B, ctl, cur, par, i, a, rank);
         if (count_live && (a.flags & 1u)) {
             const uint32_t meta = (uint32_t)a.p.w, slot = count_slot(meta, *a.Mo);
             if (sim_of(meta) == s_live_sim) atomicAdd(&s_live[slot], 1u);
-            else atomicAdd((unsigned long long*)&live_buffer(B, ctl->epoch)[a.S->counts_off + slot], 1ull);
+            else atomicAdd((unsigned long long*)&live_buffer(B, epoch)[a.S->counts_off + slot], 1ull);
         }
     }
     if (run_n && lane == 0) atomicAdd(&B.tcnt[run_tile * kTileStride], run_n);
     if (count_live) {
         __syncthreads();
         if (s_live_sim != kNone) {
-            uint64_t* L = live_buffer(B, ctl->epoch) + B.sims[s_live_sim].counts_off;
+            uint64_t* L = live_buffer(B, epoch) + B.sims[s_live_sim].counts_off;
             for (uint32_t k = threadIdx.x; k < 512; k += blockDim.x)
                 if (s_live[k]) atomicAdd((unsigned long long*)&L[k], (unsigned long long)s_live[k]);
         }
@@ -508,17 +520,86 @@ __device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_
     return prefix + total;
 }
 
+// The step's bookkeeping, run by one extra block of k_scan while the other
+// blocks scan (nothing here touches the cell arrays).  The move pass of this
+// step (epoch E, parity p) is complete: births reserved per simulation,
+// monitor sums added, released partners counted.  For every simulation:
+// births placed this step = min(reserved, limit), their prefix over the
+// simulations (births are appended after the sorted agents in simulation
+// order), the id of the first child and the new next id; the threshold
+// monitor's evaluation of the state the step started from; the step counter
+// (the step index tau in flight for the proposal search, then advanced
+// unless frozen or failed); the live counts' next-id entry.  Then the
+// buffer flips (the scatter writes the other buffer), epoch becomes E + 1,
+// and the other parity's counters are cleared for the next step.
+__device__ void bookkeeping_block(Buffers& B) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    Ctl* ctl = B.ctl;
+    const uint32_t epoch = ctl->epoch, par = epoch & 1u;
+    const uint32_t n_sims = ctl->n_sims;
+    const bool monitors = ctl->n_monitors != 0, live = ctl->live_counts != 0;
+    constexpr uint32_t kPer = (kMaxSims + kThreads - 1) / kThreads;  // simulations per thread
+    const uint32_t s0 = threadIdx.x * kPer;
+    uint32_t nb[kPer], mine = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; k++) {
+        const uint32_t s = s0 + k;
+        nb[k] = 0;
+        if (s < n_sims && B.sims[s].active) nb[k] = min(B.sims[s].nbc[par], B.bquota);
+        mine += nb[k];
+    }
+    uint32_t total;
+    uint32_t pre = block_exclusive_scan(mine, s_warp, &total);
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; k++) {
+        const uint32_t s = s0 + k;
+        if (s >= n_sims) break;
+        SimDev& S = B.sims[s];
+        B.bofs[s] = pre;
+        pre += nb[k];
+        S.nbc[par ^ 1u] = 0;
+        if (!S.active) continue;
+        const uint64_t nid = (uint64_t)S.next_id + nb[k];
+        if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
+        S.nb = nb[k];
+        S.nid0 = S.next_id;
+        S.next_id = (uint32_t)nid;
+        if (monitors) monitor_eval(B, s);  // the move pass added up the state this step started from
+        const uint32_t adv = S.step < S.max_step && S.err == 0u;
+        S.tau = S.step;
+        S.adv = adv;
+        if (adv) S.step += 1;
+        if (live)  // the last entry of a counts vector is the next id
+            live_buffer(B, epoch)[S.counts_off + S.n_counts - 1] = S.next_id;
+    }
+    if (threadIdx.x == 0) {
+        B.bofs[n_sims] = total;
+        ctl->nb_total = total;
+        ctl->cur ^= 1u;
+        ctl->epoch = epoch + 1u;
+        ctl->n_extra[par ^ 1u] = 0;
+        ctl->n_props[par] = 0;
+    }
+}
+
 // k_scan: block b scans a contiguous range of tiles; the agents before the
 // range come from the tile counts (or from k_tile_prefix on large grids).
 // The block with the last tile writes the total and the sorted-agent count.
+// The last block of the grid does the step's bookkeeping instead.
 __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     __shared__ uint32_t s_warp[kThreads / 32];
     Ctl* ctl = B.ctl;
     pdl_wait();
     if (ld_volatile(&ctl->err)) return;
+    const uint32_t nblk = gridDim.x - 1;
+    if (blockIdx.x == nblk) {
+        bookkeeping_block(B);
+        pdl_trigger();
+        return;
+    }
     const uint32_t n = ctl->n_cells;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const uint32_t per = (ntiles + nblk - 1) / nblk;
     const uint32_t t0 = min(ntiles, blockIdx.x * per), t1 = min(ntiles, t0 + per);
     if (t0 < t1) {
         const bool direct = ntiles <= kDirectTiles;
@@ -541,14 +622,15 @@ constexpr int kScatterILP = 4;
 
 __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
-    const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
-    const uint32_t n_in = ctl->n_in, total = n_in + ctl->n_extra;
-    if (bid == 0 && threadIdx.x == 0) ctl->n_props = 0;  // the move pass has consumed the old list
+    // the bookkeeping has flipped the buffers: the moved agents are in cur ^ 1
+    const uint32_t nxt = ctl->cur, cur = nxt ^ 1u;
+    const uint32_t epoch = ctl->epoch, parity = (epoch - 1u) & 1u;
+    const uint32_t n_in = ctl->n_buf[cur], total = n_in + ctl->n_extra[parity];
     // the scan has read this step's tile counts: zero them for the next step
     const uint32_t ntiles = (ctl->n_cells + kScanTile - 1) / kScanTile;
     for (uint32_t t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) B.tcnt[t * kTileStride] = 0;
     if (ctl->live_counts) {  // the live counts the next step fills (the last step's were read by now)
-        uint64_t* L = live_buffer(B, ctl->epoch + 1u);
+        uint64_t* L = live_buffer(B, epoch);
         const uint32_t n_live = ctl->n_sims * 512u;
         for (uint32_t k = bid * blockDim.x + threadIdx.x; k < n_live; k += nb * blockDim.x) L[k] = 0;
     }
@@ -641,10 +723,10 @@ __device__ __forceinline__ void consider(const SimDev& S, const ModelDev& Mo, co
     best.target = gj;
 }
 
-__device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida, uint32_t gi) {
+__device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida, uint32_t gi, uint32_t par) {
     if (best.target == kNone) return;
     atomicMin((unsigned long long*)&B.acc[best.target], (unsigned long long)((best.key & 0xFFFFFFFF00000000ull) | ida));
-    const uint32_t k = reserve(&B.ctl->n_props);  // k < capacity: at most one proposal per agent
+    const uint32_t k = reserve(&B.ctl->n_props[par]);  // k < capacity: at most one proposal per agent
     B.props[k] = make_uint2(gi, best.target);
 }
 
@@ -657,11 +739,11 @@ __device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida
 // radius lies inside that box, so the result equals the 27-cell search.
 // One chunk of sorted agents [base, base + chunk): its free agents of
 // proposing species are compacted into s_list, then each searches its box.
-__device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_t n, uint32_t* s_list,
-                                              uint32_t* s_n) {
-    const uint32_t nxt = B.ctl->cur ^ 1u;
-    const int4* __restrict__ pm = B.pm[nxt];
-    const uint32_t* __restrict__ aid = B.aid[nxt];
+__device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_t n, uint32_t par,
+                                              uint32_t* s_list, uint32_t* s_n) {
+    const uint32_t cur = B.ctl->cur;  // the sorted buffer (flipped by this step's bookkeeping)
+    const int4* __restrict__ pm = B.pm[cur];
+    const uint32_t* __restrict__ aid = B.aid[cur];
     const uint32_t* __restrict__ start = B.start;
     const uint32_t chunk = B.propose_chunk;
     // each thread takes chunk / 256 consecutive flags (4, 8 or 16 bytes, read
@@ -700,7 +782,7 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         }
         const uint32_t meta = (uint32_t)p.w;
         const SimDev& S = B.sims[sim_of(meta)];
-        if (S.step >= S.max_step) continue;  // frozen simulation
+        if (!S.adv) continue;  // frozen or failed simulation
         const ModelDev& Mo = B.models[S.model];
         const uint32_t sp = meta & M_SP;
         const uint64_t mask = Mo.sp[sp].partner_mask;
@@ -715,7 +797,7 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         // the sorted array, walked one candidate record at a time
         auto walk = [&](uint32_t a, uint32_t b) {
             for (uint32_t j = a; j < b; j++)
-                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.step, best);
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.tau, best);
         };
         if (zhi - zlo <= 1 && yhi - ylo <= 1) {
             // the usual box (2 * rmax below the cell edge): at most 2 x 2 rows,
@@ -740,123 +822,90 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
                     walk(start[row + xlo], start[row + xhi + 1]);
                 }
         }
-        claim(B, best, ida, gi);
+        claim(B, best, ida, gi, par);
     }
     __syncthreads();  // s_list and s_n are reused by the next chunk
 }
 
-__global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
-    extern __shared__ uint32_t s_list[];  // B.propose_chunk entries
-    __shared__ uint32_t s_n[1 + kThreads / 32];  // scratch of the compaction's block scan
-    pdl_wait();
-    if (ld_volatile(&B.ctl->err)) return;
-    const uint32_t n = B.ctl->n_sorted;
-    const uint32_t chunk = B.propose_chunk;
-    for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk)
-        propose_chunk(B, base, n, s_list, s_n);
-    pdl_trigger();
+// Births of this step (P6): each simulation's children, from its segment of
+// the births buffer, get ids nid0 + rank, the rank ordering them by parent
+// id (unique: at most one child per parent per step), and are appended
+// after the sorted agents, simulation after simulation.  A child is its
+// parent's moved record (end of P2: place and compartment) with the
+// parent's emitted species; it first acts at the next step.  Thread g of
+// the grid places the g-th birth of the step; the simulation it belongs to
+// comes from the births prefix (bofs, written by the bookkeeping block),
+// searched in shared memory.
+__device__ __forceinline__ void place_births(Buffers& B, uint32_t cur, uint32_t par, uint32_t nbt, uint32_t ns,
+                                             uint32_t* s_bofs) {
+    Ctl* ctl = B.ctl;
+    const uint32_t n_sims = ctl->n_sims;
+    for (uint32_t s = threadIdx.x; s <= n_sims; s += blockDim.x) s_bofs[s] = B.bofs[s];
+    __syncthreads();
+    const uint32_t src = cur ^ 1u;  // the moved (unsorted) buffer holds the parents' records
+    uint64_t* live = ctl->live_counts ? live_buffer(B, ctl->epoch - 1u) : nullptr;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nbt; g += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = n_sims;  // last s with s_bofs[s] <= g
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (s_bofs[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t s = lo, k = g - s_bofs[s], nb = s_bofs[s + 1] - s_bofs[s];
+        const uint2* seg = B.bseg + (size_t)s * B.bquota;
+        const uint32_t pid = seg[k].y;
+        uint32_t rank = 0;
+        const uint4* seg4 = reinterpret_cast<const uint4*>(seg);  // bquota is even: 16-byte aligned
+        for (uint32_t j = 0; j < nb / 2; j++) {
+            const uint4 v = seg4[j];
+            rank += (v.y < pid) + (v.w < pid);
+        }
+        if (nb & 1u) rank += seg[nb - 1].y < pid;
+        const SimDev& S = B.sims[s];
+        const ModelDev& Mo = B.models[S.model];
+        int4 q = B.pm[src][seg[k].x];
+        const uint32_t meta = (uint32_t)q.w;
+        q.w = (int)with_species(meta & ~(M_RXN | M_BOUND | M_ROLE_A), (uint32_t)Mo.sp[meta & M_SP].emit, Mo);
+        const uint32_t dst = ns + s_bofs[s] + rank;
+        B.pm[cur][dst] = q;
+        B.aid[cur][dst] = S.nid0 + rank;
+        if (live) atomicAdd((unsigned long long*)&live[S.counts_off + count_slot((uint32_t)q.w, Mo)], 1ull);
+    }
 }
 
-// ------------------------------------------------------------------------
-// Births and per-step bookkeeping, run by the last block of k_accept:
-// newborns get ids next_id + rank, the rank ordering the births of the same
-// simulation by parent id, and are appended after the sorted agents; then
-// the buffer flips and every active simulation's step counter advances.
-constexpr int kKeyTile = 1024;
-
-__device__ void finalize_block(Buffers& B) {
-    __shared__ uint64_t s_key[kKeyTile];
+__global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
+    extern __shared__ uint32_t s_list[];  // B.propose_chunk entries, then max sims + 1 birth offsets
+    __shared__ uint32_t s_n[1 + kThreads / 32];  // scratch of the compaction's block scan
+    pdl_wait();
     Ctl* ctl = B.ctl;
-    const uint32_t nxt = ctl->cur ^ 1u;
-    const uint32_t ns = ctl->n_sorted;
-    uint32_t nb = ld_volatile(&ctl->n_births);
-    if (nb > B.cap_births) nb = B.cap_births;  // the overflow was already flagged
-    if (nb && (uint64_t)ns + nb > B.cap_agents) {
-        if (threadIdx.x == 0) raise_error(ctl, ERR_CAPACITY_AGENTS, ns + nb);
-        return;
+    if (ld_volatile(&ctl->err)) return;
+    const uint32_t n = ctl->n_sorted, nbt = ctl->nb_total;
+    const uint32_t cur = ctl->cur, par = (ctl->epoch - 1u) & 1u;
+    const bool fits = (uint64_t)n + nbt <= B.cap_agents;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (fits) ctl->n_buf[cur] = n + nbt;
+        else raise_error(ctl, ERR_CAPACITY_AGENTS, n + nbt);
     }
-    // key of birth k: simulation in the high word, parent id in the low word
-    auto key_of = [&](uint32_t k) -> uint64_t {
-        return (uint64_t)(sim_of((uint32_t)B.bpm[k].w)) << 32 | B.bpar[k];
-    };
-    // rank of each birth among the births of its simulation (ids are unique:
-    // at most one birth per parent per step), and whether it is the last one
-    const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
-    constexpr int kMaxPer = (kMaxBirths + kThreads - 1) / kThreads;
-    uint32_t lt[kMaxPer], gt[kMaxPer];
-    uint64_t mine[kMaxPer];
-    for (uint32_t q = 0; q < per; q++) {
-        const uint32_t k = threadIdx.x + q * blockDim.x;
-        mine[q] = k < nb ? key_of(k) : 0;
-        lt[q] = gt[q] = 0;
-    }
-    for (uint32_t base = 0; base < nb; base += kKeyTile) {
-        const uint32_t m = min((uint32_t)kKeyTile, nb - base);
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) s_key[j] = key_of(base + j);
-        __syncthreads();
-        for (uint32_t q = 0; q < per; q++) {
-            const uint64_t key = mine[q];
-            for (uint32_t j = 0; j < m; j++) {
-                const uint64_t o = s_key[j];
-                const bool same = (o >> 32) == (key >> 32);
-                lt[q] += same & (o < key);
-                gt[q] += same & (o > key);
-            }
-        }
-    }
-    for (uint32_t q = 0; q < per; q++) {
-        const uint32_t k = threadIdx.x + q * blockDim.x;
-        if (k >= nb) continue;
-        const uint32_t s = (uint32_t)(mine[q] >> 32);
-        const uint64_t nid = (uint64_t)B.sims[s].next_id + lt[q];
-        if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
-        B.pm[nxt][ns + k] = B.bpm[k];
-        B.aid[nxt][ns + k] = (uint32_t)nid;
-        if (ctl->live_counts) {
-            const SimDev& S = B.sims[s];
-            atomicAdd((unsigned long long*)&live_buffer(B, ctl->epoch)[S.counts_off +
-                                                                       count_slot((uint32_t)B.bpm[k].w, B.models[S.model])],
-                      1ull);
-        }
-    }
-    __syncthreads();
-    for (uint32_t q = 0; q < per; q++) {
-        const uint32_t k = threadIdx.x + q * blockDim.x;
-        if (k < nb && gt[q] == 0) B.sims[mine[q] >> 32].next_id += lt[q] + 1;  // one writer per sim
-    }
-    const uint32_t n_sims = ctl->n_sims;
-    if (ctl->n_monitors)  // k_move added up the state this step started from
-        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x) monitor_eval(B, s);
-    for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
-        if (B.sims[s].active && B.sims[s].step < B.sims[s].max_step) B.sims[s].step += 1;
-    __syncthreads();
-    if (ctl->live_counts)  // the last entry of a counts vector is the next id
-        for (uint32_t s = threadIdx.x; s < n_sims; s += blockDim.x)
-            if (B.sims[s].active)
-                live_buffer(B, ctl->epoch)[B.sims[s].counts_off + B.sims[s].n_counts - 1] = B.sims[s].next_id;
-    if (threadIdx.x == 0) {
-        ctl->n_in = ns + nb;
-        ctl->n_extra = 0;
-        ctl->n_births = 0;
-        ctl->cur = nxt;
-        ctl->epoch = ctl->epoch + 1;
-    }
+    const uint32_t chunk = B.propose_chunk;
+    for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk)
+        propose_chunk(B, base, n, par, s_list, s_n);
+    if (nbt && fits) place_births(B, cur, par, nbt, n, s_list + chunk);
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------
 // k_accept: walks the proposal list; edge i -> j is final iff j's slot holds
 // i's id and nobody proposed to i.  Final edges are disjoint, so each is
-// applied without further synchronisation.  The last block to finish runs
-// the births and the step's bookkeeping.
+// applied without further synchronisation.
 __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
-    const uint32_t nxt = ctl->cur ^ 1u;
-    const uint32_t np = ctl->n_props;
-    uint64_t* live = ctl->live_counts ? live_buffer(B, ctl->epoch) : nullptr;
-    int4* __restrict__ pm = B.pm[nxt];
-    uint32_t* __restrict__ aid = B.aid[nxt];
-    uint32_t* __restrict__ apar = B.apar[nxt];
+    const uint32_t cur = ctl->cur;  // the sorted buffer
+    const uint32_t epoch = ctl->epoch, par = (epoch - 1u) & 1u;
+    const uint32_t np = ctl->n_props[par];
+    uint64_t* live = ctl->live_counts ? live_buffer(B, epoch - 1u) : nullptr;
+    int4* __restrict__ pm = B.pm[cur];
+    uint32_t* __restrict__ aid = B.aid[cur];
+    uint32_t* __restrict__ apar = B.apar[cur];
     for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += nb * blockDim.x) {
         const uint2 e = B.props[k];
         const uint32_t i = e.x, j = e.y;
@@ -898,21 +947,10 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
 }
 
 __global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
-    __shared__ bool s_last;
-    Ctl* ctl = B.ctl;
     pdl_wait();
-    if (ld_volatile(&ctl->err)) return;
+    if (ld_volatile(&B.ctl->err)) return;
     accept_pass(B, blockIdx.x, gridDim.x);
     pdl_trigger();
-    // last-block-done: every block's writes are visible to the last one
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    finalize_block(B);
-    if (threadIdx.x == 0) ctl->blocks_done = 0;
 }
 
 // ------------------------------------------------------------------------
@@ -997,7 +1035,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
     __shared__ uint32_t s_sim;
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
-    const uint32_t n = ctl->n_in;
+    const uint32_t n = ctl->n_buf[cur];
     const uint32_t chunk = ((n + gridDim.x - 1) / gridDim.x + kThreads - 1) / kThreads * kThreads;
     const uint32_t begin = blockIdx.x * chunk;
     const uint32_t end = min(n, begin + chunk);
@@ -1047,7 +1085,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
 __global__ void __launch_bounds__(kThreads) k_monitor_pass(Buffers B, uint32_t sim) {
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
-    const uint32_t n = ctl->n_in;
+    const uint32_t n = ctl->n_buf[cur];
     const SimDev& S = B.sims[sim];
     if (!S.active || !mon_due(B.mons[sim], S.step)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -1057,17 +1095,18 @@ __global__ void __launch_bounds__(kThreads) k_monitor_pass(Buffers B, uint32_t s
 __global__ void k_monitor_eval(Buffers B, uint32_t sim) { monitor_eval(B, sim); }
 
 // k_compact: between steps, copy the agents of active simulations (dropping
-// those of retired ones) to the other buffer; storage order is free.
+// those of retired ones) to the other buffer; storage order is free.  The
+// host has zeroed ctl.n_compact, which counts the agents kept.
 __global__ void __launch_bounds__(kThreads) k_compact(Buffers B) {
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur, nxt = cur ^ 1u;
-    const uint32_t n = ctl->n_in;
+    const uint32_t n = ctl->n_buf[cur];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int4 p = B.pm[cur][i];
         const uint32_t meta = (uint32_t)p.w;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
         if (!B.sims[sim_of(meta)].active) continue;
-        const uint32_t k = reserve(&ctl->n_sorted);
+        const uint32_t k = reserve(&ctl->n_compact);
         B.pm[nxt][k] = p;
         B.aid[nxt][k] = B.aid[cur][i];
         if (meta & M_BOUND) B.apar[nxt][k] = B.apar[cur][i];
@@ -1079,7 +1118,7 @@ __global__ void __launch_bounds__(kThreads) k_dump(Buffers B, int32_t sim, uint4
                                                    uint32_t cap) {
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
-    const uint32_t n = ctl->n_in;
+    const uint32_t n = ctl->n_buf[cur];
     const SimDev& S = B.sims[sim];
     const ModelDev& Mo = B.models[S.model];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1137,6 +1176,10 @@ cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B
     return cudaLaunchKernelEx(&cfg, kernel, B);
 }
 
+// Dynamic shared memory of k_propose: the chunk's proposer list, then the
+// births prefix of every simulation slot.
+size_t propose_smem(const Buffers& B) { return 4 * ((size_t)B.propose_chunk + B.max_sims + 1); }
+
 int move_blocks_per_sm() {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<false>, kThreads, 0) != cudaSuccess || n < 1) n = 4;
@@ -1146,9 +1189,9 @@ int move_blocks_per_sm() {
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool live) {
     cudaError_t e = launch_pdl(live ? k_move<true> : k_move<false>, L.blocks_agents, s, B);
     if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
-    if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_scatter, L.blocks_agents, s, B);
-    if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, 4 * (size_t)B.propose_chunk);
+    if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, propose_smem(B));
     if (e == cudaSuccess) e = launch_pdl(k_accept, L.blocks_accept, s, B);
     return e;
 }
@@ -1160,11 +1203,11 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
     cudaEventRecord(ev[1], s);
     if (L.prefix_kernel) k_tile_prefix<<<1, 1024, 0, s>>>(B);
     cudaEventRecord(ev[2], s);
-    k_scan<<<L.blocks_scan, kThreads, 0, s>>>(B);
+    k_scan<<<L.blocks_scan + 1, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[3], s);
     k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[4], s);
-    k_propose<<<L.blocks_propose, kThreads, 4 * (size_t)B.propose_chunk, s>>>(B);
+    k_propose<<<L.blocks_propose, kThreads, propose_smem(B), s>>>(B);
     cudaEventRecord(ev[5], s);
     k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[6], s);

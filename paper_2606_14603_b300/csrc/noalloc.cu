@@ -50,7 +50,7 @@ void* g_scratch_addr[kMaxDevices] = {};
 __global__ void __launch_bounds__(256) k_dump_static(Buffers B, int32_t sim, DumpScratch* sc) {
     const Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
-    const uint32_t n = ctl->n_in;
+    const uint32_t n = ctl->n_buf[cur];
     const SimDev& S = B.sims[sim];
     const ModelDev& Mo = B.models[S.model];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

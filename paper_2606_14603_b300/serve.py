@@ -9,9 +9,20 @@ its arrival to the moment its result is back on the host.
 
 The engine's arithmetic does not depend on what else is in the batch, so every
 job's result is bit-identical to the same job run alone (tests check this).
-A device error in a batch (e.g. a job whose births exceed the per-step limit)
-fails the jobs resident in that batch, which are reported with the error;
-the batch is replaced and serving goes on.
+A job whose own simulation stops with an error (births of one step beyond its
+limit) fails alone: it is reported with the error and removed, and the jobs
+sharing its batch go on.  A device error of a whole batch (e.g. its agent
+capacity exceeded) fails the jobs resident in that batch, which are reported
+with the error; the batch is replaced and serving goes on.
+
+Admission is FIFO by default (no overtaking).  With admission="backfill" a
+job that fits may be admitted ahead of an earlier one that does not, as long
+as the earliest waiting job has waited less than `backfill_limit_s`; after
+that nothing overtakes it until it is admitted (no starvation).
+
+Latency statistics cover every offered job: a job still queued or running
+when the run stops is counted at its age then (a lower bound of its
+latency), and the number of such censored jobs is reported.
 
 This is host-side orchestration over the C ABI: admission, retirement and
 epoch sizing happen here, every step runs in the engine's kernels.
@@ -95,8 +106,9 @@ class Server:
         self.molecule_steps = 0
         self.max_resident = 0
         self.waited = 0          # admissions that had to wait for capacity
-        self.failed: List[JobResult] = []   # jobs lost to a batch failure, not yet reported
+        self.failed: List[JobResult] = []   # failed jobs not yet reported
         self.batch_failures = 0
+        self.sim_failures = 0    # jobs stopped by their own simulation's error
 
     @property
     def batch(self):
@@ -179,12 +191,29 @@ class Server:
         self.steps_run += k
         return k
 
+    def _retire_failed_sims(self, g: int, now: float) -> None:
+        """Jobs of batch g whose own simulation stopped with an error: report
+        them failed and remove them; the batch and its other jobs go on."""
+        for key in [k for k in self.resident if k[0] == g]:
+            st, msg = self.batches[g].sim_status(key[1])
+            if st == 0:
+                continue
+            r = self.resident.pop(key)
+            self.failed.append(JobResult(r.job.job_id, r.job.arrival_s, r.admitted_s, now, r.job.steps,
+                                         r.job.model.n_agents, None, None, msg))
+            self.batches[g].remove(key[1])
+            self.used_agents[g] -= r.agents
+            self.used_cells[g] -= r.cells
+            self.sim_failures += 1
+
     def retire_finished(self, clock: Callable[[], float]) -> List[JobResult]:
         for g in sorted({g for (g, _) in self.resident}):
             try:
                 self.batches[g].sync()
             except AbmError as e:
                 self._fail_group(g, str(e), clock())
+                continue
+            self._retire_failed_sims(g, clock())
         done, self.failed = self.failed, []
         for key in [key for key, r in self.resident.items() if r.remaining == 0]:
             g, sid = key
@@ -211,18 +240,28 @@ class Server:
             b.close()
 
 
+def _percentile(values, q):
+    return float(np.percentile(values, q)) if len(values) else None
+
+
 def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: bool = True,
-        drain: bool = True) -> dict:
+        drain: bool = True, admission: str = "fifo", backfill_limit_s: float = 10.0) -> dict:
     """Serve `jobs` (sorted by arrival_s) and return throughput and latency
     statistics.  With real_time the arrivals follow the wall clock; otherwise
     a job arrives as soon as the server looks for new work after its arrival
-    time on a virtual clock that only advances with the GPU work done."""
+    time on a virtual clock that only advances with the GPU work done.
+    Arrivals stop at duration_s; with drain the run goes on until every
+    arrived job is done, otherwise it stops at duration_s and the jobs still
+    queued or running are censored (counted at their age then)."""
+    if admission not in ("fifo", "backfill"):
+        raise ValueError(f"unknown admission policy {admission!r}")
     pending = list(jobs)
     pending.sort(key=lambda j: j.arrival_s)
     queue: List = []                    # arrived, not admitted (FIFO by arrival)
     results: List[JobResult] = []
     rejected: List[int] = []
     waited = set()
+    overtakes = 0
     t0 = time.perf_counter()
     virtual = [0.0]
 
@@ -241,12 +280,21 @@ def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: boo
             else:
                 rejected.append(pending[i].job_id)
             i += 1
-        # admit in arrival order while they fit (no overtaking)
         if queue and not server.fits(queue[0]) and queue[0].job_id not in waited:
             waited.add(queue[0].job_id)
             server.waited += 1
+        # admit in arrival order while they fit; with backfill, later jobs that
+        # fit may pass a head that does not, until the head has waited too long
         while queue and server.fits(queue[0]):
             server.admit(queue.pop(0), clock())
+        if admission == "backfill" and queue and clock() - queue[0].arrival_s < backfill_limit_s:
+            k = 1
+            while k < len(queue):
+                if server.fits(queue[k]):
+                    server.admit(queue.pop(k), clock())
+                    overtakes += 1
+                else:
+                    k += 1
         if server.resident:
             w0 = time.perf_counter()
             server.step_epoch()
@@ -268,22 +316,37 @@ def run(jobs, server: Server, duration_s: Optional[float] = None, real_time: boo
     wall = clock()
     failed = [r for r in results if r.error is not None]
     results = [r for r in results if r.error is None]
-    lat = np.array([r.latency_s for r in results]) if results else np.zeros(0)
-    offered = sum(j.model.n_agents * j.steps for j in pending if j.arrival_s < horizon)
+    offered_jobs = [j for j in pending if j.arrival_s < horizon]
+    done_ids = {r.job_id for r in results} | {r.job_id for r in failed} | set(rejected)
+    # censored: arrived (within the window) but neither completed, failed nor rejected
+    censored = [j for j in offered_jobs if j.job_id not in done_ids and j.arrival_s <= wall]
+    lat_done = np.array([r.latency_s for r in results]) if results else np.zeros(0)
+    lat_all = np.concatenate([lat_done, np.array([wall - j.arrival_s for j in censored])]) if censored \
+        else lat_done
+    offered = sum(j.model.n_agents * j.steps for j in offered_jobs)
     return {
-        "jobs_offered": sum(1 for j in pending if j.arrival_s < horizon),
+        "jobs_offered": len(offered_jobs),
         "jobs_completed": len(results),
+        "jobs_censored": len(censored),
         "wall_s": wall,
         "throughput_molecule_steps_per_s": server.molecule_steps / wall if wall > 0 else 0.0,
         "completed_molecule_steps_per_s": sum(r.agents * r.steps for r in results) / wall if wall > 0 else 0.0,
         "jobs_per_s": len(results) / wall if wall > 0 else 0.0,
         "offered_molecule_steps_per_s": offered / horizon if math.isfinite(horizon) and horizon > 0 else None,
-        "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
-        "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
-        "latency_max_s": float(lat.max()) if len(lat) else None,
+        # over every offered job, censored ones at their age when the run stopped (lower bounds)
+        "latency_p50_s": _percentile(lat_all, 50),
+        "latency_p99_s": _percentile(lat_all, 99),
+        "latency_max_s": float(lat_all.max()) if len(lat_all) else None,
+        "latency_is_lower_bound": len(censored) > 0,
+        # over the completed jobs only
+        "completed_latency_p50_s": _percentile(lat_done, 50),
+        "completed_latency_p99_s": _percentile(lat_done, 99),
         "jobs_rejected": len(rejected),
         "jobs_failed": len(failed),
         "batch_failures": server.batch_failures,
+        "sim_failures": server.sim_failures,
+        "admission": admission,
+        "overtakes": overtakes,
         "steps_run": server.steps_run,
         "max_resident": server.max_resident,
         "admissions_waited": server.waited,

@@ -62,3 +62,56 @@ def test_births_alone_equal_the_oracle_for_60_steps(A, oracle_mod):
     assert_same_dump(sim.dump(), o.dump(), "after 60 steps")
     o.close()
     sim.close()
+
+
+def test_fifty_thousand_births_per_step_equal_the_oracle(A, oracle_mod):
+    """About 56,000 births per step in one simulation (its limit raised to
+    60,000): every child's id is next_id + its rank by parent id among
+    56k parents, ranked on the GPU in parallel; digests every step and the
+    dump at the end equal the oracle's."""
+    m, seed = W.births(40_000), 31
+    sim = A.Sim(m, seed, capacity=400_000, births_per_step=60_000)
+    o = oracle_mod.OracleSim(m, seed)
+    prev = o.counts()[-1]
+    loads = []
+    for t in range(1, 7):
+        sim.step(1)
+        o.step(1)
+        c = o.counts()
+        loads.append(int(c[-1] - prev))
+        prev = c[-1]
+        assert sim.digest() == o.digest(), f"step {t}"
+    assert min(loads[1:]) >= 50_000, loads
+    assert_same_dump(sim.dump(), o.dump(), "after 6 steps")
+    o.close()
+    sim.close()
+
+
+def test_a_simulation_over_its_births_limit_stops_alone(A, oracle_mod):
+    """Births of one step beyond a simulation's limit stop that simulation
+    only (its own error; ECAPACITY from its status and reads): the other
+    simulation of the batch goes on bit-exact, before and after the failed
+    one is removed."""
+    ok_m, bad_m = W.births(300), W.births(1000)          # ~360 and ~1,200 births per step
+    cap_a, cap_c = A.batch_capacity([ok_m, bad_m], headroom=8.0)
+    bt = A.Batch(cap_a, cap_c, 2, births_per_step=1024)
+    good, bad = bt.add(ok_m, 9), bt.add(bad_m, 10)
+    o = oracle_mod.OracleSim(ok_m, 9)
+    for t in range(1, 16):
+        bt.step(1)
+        o.step(1)
+        assert bt.digest(good) == o.digest(), f"step {t}"
+    st, msg = bt.sim_status(bad)
+    assert st == A.ECAPACITY and "births" in msg
+    with pytest.raises(A.AbmError) as e:
+        bt.counts(bad)
+    assert e.value.status == A.ECAPACITY
+    assert bt.sim_status(good) == (A.OK, "")
+    bt.remove(bad)
+    for t in range(16, 31):
+        bt.step(1)
+        o.step(1)
+        assert bt.digest(good) == o.digest(), f"step {t}"
+    assert_same_dump(bt.dump(good), o.dump(), "after 30 steps")
+    o.close()
+    bt.close()

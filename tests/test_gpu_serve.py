@@ -78,25 +78,61 @@ def test_server_rejects_jobs_that_can_never_fit():
     assert out["jobs_rejected"] == 1 and out["jobs_completed"] == 1
 
 
-def test_a_failing_batch_fails_only_its_jobs():
-    """A job whose births exceed the per-step limit makes its batch report
-    ECAPACITY: the jobs resident in that batch are reported failed, the batch
-    is replaced, and the other batch's jobs (and later jobs) complete, equal
-    to their alone runs."""
+def test_a_failing_job_fails_alone_in_a_shared_batch():
+    """A job whose births in one step exceed its limit stops with its own
+    error (its simulation is frozen, reported failed and removed); the
+    healthy job resident in the same batch, and a later job admitted into
+    it, complete equal to their alone runs and to the oracle."""
     require_gpu()
     A = engine()
     from paper_2606_14603_b300 import serve
+    import oracle
     flood = W.Model("flood", [W.Species("G", 20_000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
                     [W.Compartment(W.CUBE, 2.0)])
     jobs = [W.Job(0, 0.000, W.mapk(12_000), 3, 80),
             W.Job(1, 0.001, flood, 4, 30),
             W.Job(2, 0.050, W.mapk(9_000, drug_frac=0.0), 5, 60)]
     caps = [A.model_grid(j.model)[1] for j in jobs]
+    srv = serve.Server(capacity_agents=80_000, capacity_cells=4 * max(caps), max_sims=3, epoch=20, groups=1)
+    out = serve.run(jobs, srv, real_time=False)
+    srv.close()
+    assert out["jobs_failed"] == 1 and out["batch_failures"] == 0 and out["sim_failures"] == 1
+    assert [r.job_id for r in out["failed"]] == [1] and "births" in out["failed"][0].error
+    assert sorted(r.job_id for r in out["results"]) == [0, 2]
+    assert out["max_resident"] >= 2                       # the failing job shared the batch
+    for r in out["results"]:
+        j = jobs[r.job_id]
+        alone = A.Sim(j.model, j.seed)
+        alone.step(j.steps)
+        assert r.digest == alone.digest(), f"job {j.job_id}"
+        assert np.array_equal(r.counts, alone.counts()), f"job {j.job_id}"
+        alone.close()
+        o = oracle.OracleSim(j.model, j.seed)
+        o.step(j.steps)
+        assert r.digest == o.digest(), f"job {j.job_id} vs the oracle"
+        o.close()
+
+
+def test_a_failing_batch_fails_only_its_jobs():
+    """A job that overflows its batch's agent capacity (births within its
+    own limit, but more agents than the batch holds) makes that batch report
+    ECAPACITY: the jobs resident in that batch are reported failed, the batch
+    is replaced, and the other batch's jobs (and later jobs) complete, equal
+    to their alone runs."""
+    require_gpu()
+    A = engine()
+    from paper_2606_14603_b300 import serve
+    grow = W.Model("grow", [W.Species("G", 9_000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
+                   [W.Compartment(W.CUBE, 2.0)])
+    jobs = [W.Job(0, 0.000, W.mapk(12_000), 3, 80),
+            W.Job(1, 0.001, grow, 4, 30),
+            W.Job(2, 0.050, W.mapk(9_000, drug_frac=0.0), 5, 60)]
+    caps = [A.model_grid(j.model)[1] for j in jobs]
     srv = serve.Server(capacity_agents=2 * 40_000, capacity_cells=4 * max(caps), max_sims=2, epoch=20, groups=2)
     out = serve.run(jobs, srv, real_time=False)
     srv.close()
     assert out["jobs_failed"] == 1 and out["batch_failures"] == 1
-    assert [r.job_id for r in out["failed"]] == [1] and "births" in out["failed"][0].error
+    assert [r.job_id for r in out["failed"]] == [1] and "agent capacity" in out["failed"][0].error
     assert sorted(r.job_id for r in out["results"]) == [0, 2]
     for r in out["results"]:
         j = jobs[r.job_id]
@@ -104,3 +140,49 @@ def test_a_failing_batch_fails_only_its_jobs():
         alone.step(j.steps)
         assert r.digest == alone.digest(), f"job {j.job_id}"
         alone.close()
+
+
+def test_backfill_lets_small_jobs_pass_a_large_one_and_stays_exact():
+    """Backfill admission: a large job that does not fit yet is passed by
+    small ones that do (overtakes counted); every result still equals its
+    alone run, and FIFO on the same jobs admits in arrival order."""
+    require_gpu()
+    A = engine()
+    from paper_2606_14603_b300 import serve
+    jobs = [W.Job(0, 0.000, W.mapk(30_000), 3, 60),
+            W.Job(1, 0.001, W.mapk(30_000, drug_frac=0.0), 4, 40),     # does not fit next to job 0
+            W.Job(2, 0.002, W.toy(600, 500, edge_um=0.4), 5, 50),     # fits next to job 0
+            W.Job(3, 0.003, W.toy(700, 400, edge_um=0.4), 6, 30)]
+    caps = [A.model_grid(j.model)[1] for j in jobs]
+    res = {}
+    for policy in ("fifo", "backfill"):
+        srv = serve.Server(capacity_agents=50_000, capacity_cells=3 * max(caps), max_sims=4, epoch=10, groups=1)
+        res[policy] = serve.run(jobs, srv, real_time=False, admission=policy, backfill_limit_s=1e9)
+        srv.close()
+        assert res[policy]["jobs_completed"] == 4 and res[policy]["jobs_censored"] == 0
+    assert res["fifo"]["overtakes"] == 0 and res["backfill"]["overtakes"] >= 1
+    done_fifo = {r.job_id: r.finished_s for r in res["fifo"]["results"]}
+    done_bf = {r.job_id: r.finished_s for r in res["backfill"]["results"]}
+    assert done_bf[2] < done_fifo[2]                       # the small job no longer waits for job 1
+    by_id = {r.job_id: r for r in res["backfill"]["results"]}
+    for j in jobs:
+        alone = A.Sim(j.model, j.seed)
+        alone.step(j.steps)
+        assert by_id[j.job_id].digest == alone.digest(), f"job {j.job_id}"
+        alone.close()
+
+
+def test_censored_jobs_count_in_the_latency():
+    """Stopping at the horizon without draining: jobs still queued or running
+    are counted at their age (lower bounds) and reported as censored."""
+    require_gpu()
+    engine()
+    from paper_2606_14603_b300 import serve
+    jobs = [W.Job(k, 0.001 * k, W.mapk(20_000), k + 1, 4000) for k in range(4)]
+    srv = serve.Server(capacity_agents=30_000, capacity_cells=4 * 30_000, max_sims=2, epoch=50, groups=1)
+    out = serve.run(jobs, srv, duration_s=0.05, real_time=False, drain=False)
+    srv.close()
+    assert out["jobs_offered"] == 4
+    assert out["jobs_completed"] + out["jobs_censored"] + out["jobs_failed"] == 4
+    assert out["jobs_censored"] >= 1 and out["latency_is_lower_bound"]
+    assert out["latency_max_s"] >= max(0.0, out["wall_s"] - 0.003)
