@@ -54,6 +54,8 @@ def parse():
                    help="steps of the 4M/16M-agent cascade summary (0 = skip)")
     p.add_argument("--volume-steps", type=int, default=4000,
                    help="steps of the volume-invariance summary (1M vs 10M agents per dose; 0 = skip)")
+    p.add_argument("--births-steps", type=int, default=20,
+                   help="steps of the birth-heavy summary (about 50k-60k births per step; 0 = skip)")
     p.add_argument("--agents", type=int, default=0, help="override the agent count")
     p.add_argument("--profile-steps", type=int, default=50)
     p.add_argument("--no-flush", action="store_true", help="do not flush L2 between steps")
@@ -595,6 +597,26 @@ def main():
                           "l2": "flushed between steps"})
             bs.close()
 
+    births = None
+    if args.births_steps > 0 and args.workload == "cascade" and not args.agents:
+        import workloads as W
+        bm = W.births(50_000)
+        bsim = A.Sim(bm, 31, capacity=1_000_000, births_per_step=80_000, stream=stream)
+        bsim.step(5)
+        c0 = bsim.counts()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bsim.step(args.births_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c1 = bsim.counts()
+        ms = e0.elapsed_time(e1) / args.births_steps
+        births = {"model": "births(50,000 expressors, p_emit 1; children emit and degrade)",
+                  "steps": args.births_steps, "ms_per_step": ms,
+                  "births_per_step": float(c1[-1] - c0[-1]) / args.births_steps,
+                  "agents_live": molecules(c1, bm), "l2": "not flushed (state below L2)"}
+        bsim.close()
+
     volume = None
     if args.volume_steps > 0 and args.workload == "cascade" and not args.agents:
         from paper_2606_14603_b300.experiments import volume_invariance
@@ -619,7 +641,7 @@ def main():
             "roofline": roof, "step_roofline": step_roof,
             "kernel_share": share, "kernel_ms_per_step": {k: v / P for k, v in prof.items()},
             "gpu_launches": launches_per_step(sim_cells) * K, "e2e": e2e, "cpu_baseline": cpu, "sweep": sweep,
-            "serve": served, "serve_subcapacity": served_sub, "sizes": sizes, "volume": volume,
+            "serve": served, "serve_subcapacity": served_sub, "sizes": sizes, "births": births, "volume": volume,
             "clocks": clocks, "wall_s_timed_region": wall}
     if rank == 0:
         print(json.dumps(line), flush=True)

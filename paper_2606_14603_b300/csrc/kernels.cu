@@ -158,7 +158,7 @@ __device__ __forceinline__ void monitor_eval(Buffers& B, uint32_t s) {
 
 // Phase 1: P1 events (a released partner is moved and placed right away:
 // rare) and the move draw; issues the three table loads.
-__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t par, uint32_t i,
+__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t parity, uint32_t i,
                                             MoveState& a) {
     uint32_t meta = (uint32_t)a.p.w;
     a.flags = 0;
@@ -187,7 +187,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, 
                 int4 q = a.p;
                 q.w = (int)with_species(meta, (uint32_t)hprod, Mo);
                 brownian_move(S, Mo.sp[hprod], B.ztab, q, par, t);
-                const uint32_t k = reserve(&ctl->n_extra[par]);
+                const uint32_t k = reserve(&ctl->n_extra[parity]);
                 if (k < B.cap_extras) {
                     const uint32_t key = cell_of(S, q.x, q.y, q.z);
                     const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
@@ -267,12 +267,12 @@ __device__ __forceinline__ void move_phase2(MoveState& a) {
 // (the parent's slot in the moved buffer, its id).  The lanes of one
 // simulation reserve together; beyond the simulation's limit its own error
 // word is set (the simulation stops, the others go on).
-__device__ __noinline__ void reserve_birth(Buffers& B, Ctl* ctl, uint32_t par, uint32_t sim, uint32_t slot,
+__device__ __noinline__ void reserve_birth(Buffers& B, Ctl* ctl, uint32_t parity, uint32_t sim, uint32_t slot,
                                               uint32_t id) {
     cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), (int)sim);
     SimDev& S = B.sims[sim];
     uint32_t base = 0;
-    if (grp.thread_rank() == 0) base = atomicAdd(&S.nbc[par], grp.size());
+    if (grp.thread_rank() == 0) base = atomicAdd(&S.nbc[parity], grp.size());
     const uint32_t k = grp.shfl(base, 0) + grp.thread_rank();
     if (k < B.bquota) {
         B.bseg[(size_t)sim * B.bquota + k] = make_uint2(slot, id);
@@ -283,7 +283,7 @@ __device__ __noinline__ void reserve_birth(Buffers& B, Ctl* ctl, uint32_t par, u
 }
 
 // Phase 4: results (the histogram rank comes from the atomic between) and births.
-__device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t par, uint32_t i,
+__device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t parity, uint32_t i,
                                             const MoveState& a, uint32_t rank) {
     if (!(a.flags & 1u)) {
         B.rk[i] = kNone;
@@ -291,7 +291,7 @@ __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, 
     }
     B.rk[i] = rank;  // the scatter finds the cell again from the moved record
     B.pm[cur][i] = a.p;
-    if (a.flags & 2u) reserve_birth(B, ctl, par, sim_of((uint32_t)a.p.w), i, a.id);
+    if (a.flags & 2u) reserve_birth(B, ctl, parity, sim_of((uint32_t)a.p.w), i, a.id);
 }
 
 
@@ -300,11 +300,12 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
     const uint32_t n = ctl->n_buf[cur];
-    const uint32_t epoch = ctl->epoch, par = epoch & 1u;
+    const uint32_t epoch = ctl->epoch, parity = epoch & 1u;
+    if (bid == 0 && threadIdx.x == 0) ctl->n_sorted = 0;  // the scan writes the count (if any cell is in use)
     const int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
     // proposal slots touched last step become empty again (the list is short)
-    const uint32_t np = ctl->n_props[par ^ 1u];
+    const uint32_t np = ctl->n_props[parity ^ 1u];
     const uint32_t stride = nb * blockDim.x;
     for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
     // threshold monitors add up the records as they stand after t steps (a
@@ -356,7 +357,7 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
             nx_id = aid[i + 32];
         }
         if (i < wend) {
-            move_phase1(B, ctl, cur, par, i, a);
+            move_phase1(B, ctl, cur, parity, i, a);
             move_phase2(a);
         }
         const uint32_t rank = (a.flags & 1u) ? atomicAdd(&B.cnt[a.key], 1u) : 0u;
@@ -373,7 +374,7 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
             run_n += __popc(same);
             if (tile != kNone && tile != t0) atomicAdd(&B.tcnt[tile * kTileStride], 1u);
         }
-        if (i < wend) move_phase4(B, ctl, cur, par, i, a, rank);
+        if (i < wend) move_phase4(B, ctl, cur, parity, i, a, rank);
         if (count_live && (a.flags & 1u)) {
             const uint32_t meta = (uint32_t)a.p.w, slot = count_slot(meta, *a.Mo);
             if (sim_of(meta) == s_live_sim) atomicAdd(&s_live[slot], 1u);
@@ -535,7 +536,7 @@ __device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_
 __device__ void bookkeeping_block(Buffers& B) {
     __shared__ uint32_t s_warp[kThreads / 32];
     Ctl* ctl = B.ctl;
-    const uint32_t epoch = ctl->epoch, par = epoch & 1u;
+    const uint32_t epoch = ctl->epoch, parity = epoch & 1u;
     const uint32_t n_sims = ctl->n_sims;
     const bool monitors = ctl->n_monitors != 0, live = ctl->live_counts != 0;
     constexpr uint32_t kPer = (kMaxSims + kThreads - 1) / kThreads;  // simulations per thread
@@ -545,7 +546,7 @@ __device__ void bookkeeping_block(Buffers& B) {
     for (uint32_t k = 0; k < kPer; k++) {
         const uint32_t s = s0 + k;
         nb[k] = 0;
-        if (s < n_sims && B.sims[s].active) nb[k] = min(B.sims[s].nbc[par], B.bquota);
+        if (s < n_sims && B.sims[s].active) nb[k] = min(B.sims[s].nbc[parity], B.bquota);
         mine += nb[k];
     }
     uint32_t total;
@@ -557,8 +558,11 @@ __device__ void bookkeeping_block(Buffers& B) {
         SimDev& S = B.sims[s];
         B.bofs[s] = pre;
         pre += nb[k];
-        S.nbc[par ^ 1u] = 0;
-        if (!S.active) continue;
+        S.nbc[parity ^ 1u] = 0;
+        if (!S.active) {
+            S.adv = 0;
+            continue;
+        }
         const uint64_t nid = (uint64_t)S.next_id + nb[k];
         if (nid >= kNone) raise_error(ctl, ERR_ID_SPACE, s);
         S.nb = nb[k];
@@ -577,8 +581,8 @@ __device__ void bookkeeping_block(Buffers& B) {
         ctl->nb_total = total;
         ctl->cur ^= 1u;
         ctl->epoch = epoch + 1u;
-        ctl->n_extra[par ^ 1u] = 0;
-        ctl->n_props[par] = 0;
+        ctl->n_extra[parity ^ 1u] = 0;
+        ctl->n_props[parity] = 0;
     }
 }
 
@@ -723,10 +727,10 @@ __device__ __forceinline__ void consider(const SimDev& S, const ModelDev& Mo, co
     best.target = gj;
 }
 
-__device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida, uint32_t gi, uint32_t par) {
+__device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida, uint32_t gi, uint32_t parity) {
     if (best.target == kNone) return;
     atomicMin((unsigned long long*)&B.acc[best.target], (unsigned long long)((best.key & 0xFFFFFFFF00000000ull) | ida));
-    const uint32_t k = reserve(&B.ctl->n_props[par]);  // k < capacity: at most one proposal per agent
+    const uint32_t k = reserve(&B.ctl->n_props[parity]);  // k < capacity: at most one proposal per agent
     B.props[k] = make_uint2(gi, best.target);
 }
 
@@ -739,7 +743,7 @@ __device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida
 // radius lies inside that box, so the result equals the 27-cell search.
 // One chunk of sorted agents [base, base + chunk): its free agents of
 // proposing species are compacted into s_list, then each searches its box.
-__device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_t n, uint32_t par,
+__device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_t n, uint32_t parity,
                                               uint32_t* s_list, uint32_t* s_n) {
     const uint32_t cur = B.ctl->cur;  // the sorted buffer (flipped by this step's bookkeeping)
     const int4* __restrict__ pm = B.pm[cur];
@@ -822,7 +826,7 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
                     walk(start[row + xlo], start[row + xhi + 1]);
                 }
         }
-        claim(B, best, ida, gi, par);
+        claim(B, best, ida, gi, parity);
     }
     __syncthreads();  // s_list and s_n are reused by the next chunk
 }
@@ -836,7 +840,7 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
 // the grid places the g-th birth of the step; the simulation it belongs to
 // comes from the births prefix (bofs, written by the bookkeeping block),
 // searched in shared memory.
-__device__ __forceinline__ void place_births(Buffers& B, uint32_t cur, uint32_t par, uint32_t nbt, uint32_t ns,
+__device__ __forceinline__ void place_births(Buffers& B, uint32_t cur, uint32_t nbt, uint32_t ns,
                                              uint32_t* s_bofs) {
     Ctl* ctl = B.ctl;
     const uint32_t n_sims = ctl->n_sims;
@@ -880,7 +884,7 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     Ctl* ctl = B.ctl;
     if (ld_volatile(&ctl->err)) return;
     const uint32_t n = ctl->n_sorted, nbt = ctl->nb_total;
-    const uint32_t cur = ctl->cur, par = (ctl->epoch - 1u) & 1u;
+    const uint32_t cur = ctl->cur, parity = (ctl->epoch - 1u) & 1u;
     const bool fits = (uint64_t)n + nbt <= B.cap_agents;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (fits) ctl->n_buf[cur] = n + nbt;
@@ -888,8 +892,8 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     }
     const uint32_t chunk = B.propose_chunk;
     for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk)
-        propose_chunk(B, base, n, par, s_list, s_n);
-    if (nbt && fits) place_births(B, cur, par, nbt, n, s_list + chunk);
+        propose_chunk(B, base, n, parity, s_list, s_n);
+    if (nbt && fits) place_births(B, cur, nbt, n, s_list + chunk);
     pdl_trigger();
 }
 
@@ -900,8 +904,8 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
 __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;  // the sorted buffer
-    const uint32_t epoch = ctl->epoch, par = (epoch - 1u) & 1u;
-    const uint32_t np = ctl->n_props[par];
+    const uint32_t epoch = ctl->epoch, parity = (epoch - 1u) & 1u;
+    const uint32_t np = ctl->n_props[parity];
     uint64_t* live = ctl->live_counts ? live_buffer(B, epoch - 1u) : nullptr;
     int4* __restrict__ pm = B.pm[cur];
     uint32_t* __restrict__ aid = B.aid[cur];

@@ -122,8 +122,8 @@ def test_a_failing_batch_fails_only_its_jobs():
     require_gpu()
     A = engine()
     from paper_2606_14603_b300 import serve
-    grow = W.Model("grow", [W.Species("G", 9_000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
-                   [W.Compartment(W.CUBE, 2.0)])
+    grow = W.Model("grow", [W.Species("G", 8_000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
+                   [W.Compartment(W.CUBE, 2.0)])                 # 8,000 births a step: within its limit
     jobs = [W.Job(0, 0.000, W.mapk(12_000), 3, 80),
             W.Job(1, 0.001, grow, 4, 30),
             W.Job(2, 0.050, W.mapk(9_000, drug_frac=0.0), 5, 60)]
@@ -149,10 +149,10 @@ def test_backfill_lets_small_jobs_pass_a_large_one_and_stays_exact():
     require_gpu()
     A = engine()
     from paper_2606_14603_b300 import serve
-    jobs = [W.Job(0, 0.000, W.mapk(30_000), 3, 60),
-            W.Job(1, 0.001, W.mapk(30_000, drug_frac=0.0), 4, 40),     # does not fit next to job 0
-            W.Job(2, 0.002, W.toy(600, 500, edge_um=0.4), 5, 50),     # fits next to job 0
-            W.Job(3, 0.003, W.toy(700, 400, edge_um=0.4), 6, 30)]
+    jobs = [W.Job(0, 0.0, W.mapk(30_000), 3, 60),
+            W.Job(1, 0.0, W.mapk(30_000, drug_frac=0.0), 4, 40),     # does not fit next to job 0
+            W.Job(2, 0.0, W.toy(600, 500, edge_um=0.4), 5, 50),     # fits next to job 0
+            W.Job(3, 0.0, W.toy(700, 400, edge_um=0.4), 6, 30)]
     caps = [A.model_grid(j.model)[1] for j in jobs]
     res = {}
     for policy in ("fifo", "backfill"):
