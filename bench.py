@@ -32,8 +32,6 @@ STEP_BYTES_PER_AGENT = 40
 E2E_STEPS = 500          # steps of the end-to-end loop (creation amortised over them)
 KERNEL_BYTES = {"k_move": (40, "agent"), "k_tile_prefix": (8 / 8192, "cell"), "k_scan": (12, "cell"),
                 "k_scatter": (53, "agent"), "k_propose": (24, "agent"), "k_accept": (4, "agent")}
-# k_accept reads 0 in the per-kernel profile: a step's acceptance runs inside
-# the next step's k_move (agents named by the proposal list are moved there)
 
 
 def parse():
@@ -167,10 +165,9 @@ def kernel_source_sha():
 
 
 def launches_per_step(cells):
-    """Engine kernels one step launches: four (k_move, k_scan, k_scatter,
-    k_propose), plus k_tile_prefix on grids of more than 8192 scan tiles of
-    8192 cells."""
-    return 4 + (1 if (cells + 8191) // 8192 > 8192 else 0)
+    """Engine kernels one step launches: five, plus k_tile_prefix on grids of
+    more than 8192 scan tiles of 8192 cells."""
+    return 5 + (1 if (cells + 8191) // 8192 > 8192 else 0)
 
 
 def ncu_traffic(kernel):

@@ -126,7 +126,7 @@ typedef struct {
 typedef struct {
     uint64_t       capacity_agents;  /* slots shared by all sims (> 0)     */
     uint64_t       capacity_cells;   /* grid cells shared by all sims      */
-    uint32_t       max_sims;         /* 1..1024                            */
+    uint32_t       max_sims;         /* 1..2048                            */
     uint32_t       births_per_step;  /* births one step may add to EACH
                                         simulation (its segment of the births
                                         buffer, 8 bytes per birth and slot);
@@ -348,9 +348,7 @@ abm_status  abm_dump_noalloc(abm_sim* sim, abm_record* out, size_t cap, size_t* 
  * before and after each of the step's kernels, and writes the summed time of
  * each kernel in milliseconds to kernel_ms[0..5] (n_kernels >= 6; names from
  * abm_kernel_name; slot 1, k_tile_prefix, runs only on grids of more than
- * 8192 tiles of 8192 cells and reads 0 otherwise; slot 5, the acceptance of
- * a step's proposals, reads 0: it runs inside the next step's k_move, or as
- * a flush before the host reads the state).  Synchronous.  The state
+ * 8192 tiles of 8192 cells and reads 0 otherwise).  Synchronous.  The state
  * advances exactly as abm_step. */
 abm_status  abm_profile_step(abm_sim* sim, uint32_t n, float* kernel_ms, uint32_t n_kernels);
 abm_status  abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, uint32_t n_kernels);

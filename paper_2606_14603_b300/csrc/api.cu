@@ -318,7 +318,6 @@ struct abm_batch {
     uint32_t epoch_host = 1;             // device epoch after the steps issued so far
     uint32_t live_on = 0;                // host copy of ctl.live_counts (source of its upload)
     bool live_valid = false;             // live counts hold the current state (a step ran with them on)
-    bool pending = false;                // the last step's acceptance awaits the next move pass (or a flush)
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;
     cudaGraphExec_t g1_live = nullptr, g8_live = nullptr;  // the same with live counts, captured on first use
     uint32_t sim_errs_seen = 0;          // per-simulation errors already read from the device
@@ -451,16 +450,6 @@ abm_status sync_and_check(abm_batch* b, Ctl* out_ctl = nullptr) {
     const Ctl h = *b->h_ctl;
     if (out_ctl) *out_ctl = h;
     return check_ctl(b, h);
-}
-
-// Applies the last step's pending acceptance before the state is read or
-// changed between steps (stream-ordered; no synchronisation).
-abm_status flush(abm_batch* b) {
-    if (!b->pending) return ABM_OK;
-    CU(launch_flush(b->B, b->L, b->stream));
-    CU(cudaMemsetAsync(&b->B.ctl->pending, 0, 4, b->stream));
-    b->pending = false;
-    return ABM_OK;
 }
 
 // The status of a simulation whose per-simulation error has been read
@@ -829,8 +818,6 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
         }
         c->n0 = rs.pm.size();  // agents to place
     }
-    st = flush(b);  // compaction and admission change the slots the pending acceptance names
-    if (st != ABM_OK) return st;
     Ctl h;
     st = sync_and_check(b, &h);
     if (st != ABM_OK) {
@@ -1025,8 +1012,6 @@ abm_status abm_batch_monitor_read(abm_batch* b, int32_t sim, abm_monitor_state* 
         b->err = "monitor: no threshold monitor on this simulation";
         return ABM_ESTATE;
     }
-    abm_status fst = flush(b);
-    if (fst != ABM_OK) return fst;
     CU(launch_monitor(b->B, b->L, b->stream, sim));
     MonDev M;
     std::vector<int64_t> ring(kMonTrace);
@@ -1079,7 +1064,6 @@ abm_status abm_batch_step(abm_batch* b, uint32_t n) {
     if (steps) {
         b->epoch_host += steps;
         b->live_valid = b->live_on != 0;
-        b->pending = true;
     }
     return ABM_OK;
 }
@@ -1108,7 +1092,6 @@ abm_status abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, ui
     if (n) {
         b->epoch_host += n;
         b->live_valid = b->live_on != 0;
-        b->pending = true;
     }
     for (int k = 0; k < kStepKernels; k++) kernel_ms[k] = (float)acc[k];
     return sync_and_check(b);
@@ -1138,8 +1121,6 @@ abm_status abm_batch_live_agents(abm_batch* b, uint64_t* out) {
 static abm_status observe(abm_batch* b, int32_t sim, int want_digest) {
     if (b->failed) return ABM_ESTATE;
     if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
-    abm_status st = flush(b);
-    if (st != ABM_OK) return st;
     CU(cudaMemsetAsync(b->B.counts + (size_t)sim * 512, 0, 8 * 512, b->stream));
     if (want_digest) CU(cudaMemsetAsync(b->B.digests + sim, 0, 8, b->stream));
     CU(launch_observe(b->B, b->L, b->stream, sim, want_digest));
@@ -1167,10 +1148,8 @@ abm_status abm_batch_counts_begin(abm_batch* b, int32_t sim, uint32_t slot) {
     if (!b || slot >= ABM_READ_SLOTS || b->rs[slot].pending) return ABM_EINVAL;
     if (b->failed) return ABM_ESTATE;
     if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
-    // live counts of the last step's result when they hold the current state
-    // (its acceptance applied first), else a pass over the agents
-    abm_status fst = flush(b);
-    if (fst != ABM_OK) return fst;
+    // live counts of the last step's result when they hold the current state,
+    // else a pass over the agents
     const uint64_t* src = b->B.live + (size_t)((b->epoch_host - 1u) & 1u) * b->B.live_stride;
     if (!b->live_valid) {
         abm_status st = observe(b, sim, 0);
@@ -1234,10 +1213,8 @@ abm_status abm_batch_dump(abm_batch* b, int32_t sim, abm_record* out, size_t cap
     if (!b) return ABM_EINVAL;
     if (b->failed) return ABM_ESTATE;
     if (sim < 0 || (uint32_t)sim >= b->max_sims || b->sims[sim].state != 1) return ABM_ESTATE;
-    abm_status st = flush(b);
-    if (st != ABM_OK) return st;
     Ctl h;
-    st = sync_and_check(b, &h);
+    abm_status st = sync_and_check(b, &h);
     if (st == ABM_OK) st = sim_status(b, sim);
     if (st != ABM_OK) return st;
     const uint32_t dcap = (uint32_t)std::min<uint64_t>(2ull * h.n_buf[h.cur] + 1, 0xFFFFFFF0ull);
@@ -1513,9 +1490,6 @@ bool internal_view(abm_sim* s, Buffers* B, Launch* L, cudaStream_t* stream, int3
     *device = s->b->device;
     return true;
 }
-
-// Applies a pending acceptance before another translation unit reads the state.
-abm_status internal_flush(abm_sim* s) { return flush(s->b); }
 
 // A CUDA failure seen by another translation unit: the handle becomes
 // destroy-only, exactly as after a failure inside this file.

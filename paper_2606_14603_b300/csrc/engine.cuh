@@ -28,18 +28,8 @@
 //
 // meta word: bits 0-5 species, 6-7 compartment, 8 carrier, 9 carrier is
 // reactant a, 10 dead, 11 absorbed (became hidden this step), 12-19 reaction
-// of the complex, 20-29 simulation slot, 30 named by the proposal list
-// (M_WALK), 31 the species proposes (kept in step with every change of
-// species).
-//
-// Acceptance of a step's proposals (P5) is applied by the next step's move
-// pass: its main loop skips the agents marked M_WALK, and list entries move
-// them after applying the final edges -- a targeted agent by the entry that
-// won its slot (its own proposal, if any, cannot be final), a proposer
-// nobody targeted by its own entry; both decided from acc, which the move
-// pass does not write.  Between steps the acceptance is pending
-// (ctl.pending); the host applies it with a flush kernel before any read or
-// change of the state.
+// of the complex, 20-30 simulation slot, 31 the species proposes (kept in
+// step with every change of species).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -49,7 +39,7 @@ namespace abm {
 constexpr int kMaxSpecies = 64;
 constexpr int kMaxReactions = 255;
 constexpr int kMaxComp = 4;
-constexpr int kMaxSims = 1024;
+constexpr int kMaxSims = 2048;
 constexpr uint32_t kDefaultBirths = 8192;   // default births per step of one simulation
 constexpr int kScanTile = 8192;           // cells per scan tile (256 threads x 32)
 constexpr int kTileStride = 32;           // words between two tile counters
@@ -65,13 +55,8 @@ constexpr uint32_t M_ROLE_A = 1u << 9;
 constexpr uint32_t M_DEAD = 1u << 10;
 constexpr uint32_t M_ABSORBED = 1u << 11;
 constexpr uint32_t M_RXN_SHIFT = 12, M_RXN = 0xFFu << 12;
-constexpr uint32_t M_SIM_SHIFT = 20, M_SIM_MASK = 0x3FFu;
+constexpr uint32_t M_SIM_SHIFT = 20, M_SIM_MASK = 0x7FFu;
 constexpr uint32_t M_PROP = 1u << 31;       // free agent of a species that proposes
-// An agent the step's proposal list names (a proposer with a claim or a
-// target): its acceptance is applied, and it is moved, by the list walk of
-// the next move pass, whose main loop skips it.  Set by the proposal search,
-// kept on the moved record, stripped by the scatter (or by a flush).
-constexpr uint32_t M_WALK = 1u << 30;
 
 // device error codes (ctl.err); mapped to abm_status on the host
 enum : uint32_t {
@@ -174,9 +159,7 @@ struct Ctl {
     uint32_t live_counts;    // 1: each step leaves the counts of its result in live[epoch & 1]
     uint32_t n_compact;      // agents kept by a compaction (between steps)
     uint32_t sim_errs;       // simulations that raised a per-simulation error
-    uint32_t pending;        // 1: the last step's acceptance is not applied yet
-    uint32_t walk_next;      // next list entry a move-pass warp takes
-    uint32_t pad;
+    uint32_t pad[3];
 };
 
 struct Buffers {
@@ -341,10 +324,7 @@ cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool 
 cudaError_t launch_init(const Buffers& B, const Launch& L, cudaStream_t s, uint32_t sim,
                         uint32_t base, uint32_t n0, const uint32_t* d_species_end, uint32_t n_sp);
 cudaError_t launch_observe(const Buffers& B, const Launch& L, cudaStream_t s, int32_t only_sim, int want_digest);
-// Applies a pending acceptance (between steps; the host then clears ctl.pending).
-cudaError_t launch_flush(const Buffers& B, const Launch& L, cudaStream_t s);
-// The step with a CUDA event before and after each of its kernels (ev[0..6];
-// slot 5, the acceptance, is applied inside the next move pass and reads 0).
+// The step with a CUDA event before and after each of its kernels (ev[0..6]).
 constexpr int kStepKernels = 6;
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev,
                               bool live = false);

@@ -1,8 +1,8 @@
 // kernels.cu — the per-step CUDA kernels (sm_103a) of the molecule-agent engine.
 //
 // One step (paper Sec. 2: diffusion, proximity binding, product release,
-// expression, degradation, compartment migration) is four launches over the
-// whole batch of simulations (five on grids of more than 8192 scan tiles),
+// expression, degradation, compartment migration) is five launches over the
+// whole batch of simulations (six on grids of more than 8192 scan tiles),
 // all reading their sizes from the device control block so that a captured
 // CUDA graph replays them unchanged:
 //
@@ -18,10 +18,7 @@
 //   k_propose   neighbour query over the cells a contact radius can reach,
 //               nearest eligible partner, atomicMin on a packed key; births
 //               ranked by parent id and placed after the sorted agents
-//
-// The acceptance of a step's proposals (final-edge rule and reaction
-// application) is applied by the next step's k_move, or by k_flush when the
-// host reads the state between steps: four launches per step.
+//   k_accept    final-edge rule and reaction application
 //
 // The engine never depends on storage order: every decision is a function
 // of the set of (id, state) pairs, so atomics may run in any order.
@@ -161,7 +158,8 @@ __device__ __forceinline__ void monitor_eval(Buffers& B, uint32_t s) {
 
 // Phase 1: P1 events (a released partner is moved and placed right away:
 // rare) and the move draw; issues the three table loads.
-__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, MoveState& a) {
+__device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t parity, uint32_t i,
+                                            MoveState& a) {
     uint32_t meta = (uint32_t)a.p.w;
     a.flags = 0;
     if (meta & (M_DEAD | M_ABSORBED)) return;
@@ -189,7 +187,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, 
                 int4 q = a.p;
                 q.w = (int)with_species(meta, (uint32_t)hprod, Mo);
                 brownian_move(S, Mo.sp[hprod], B.ztab, q, par, t);
-                const uint32_t k = reserve(&ctl->n_extra[ctl->epoch & 1u]);  // (rare: read here)
+                const uint32_t k = reserve(&ctl->n_extra[parity]);
                 if (k < B.cap_extras) {
                     const uint32_t key = cell_of(S, q.x, q.y, q.z);
                     const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
@@ -269,10 +267,10 @@ __device__ __forceinline__ void move_phase2(MoveState& a) {
 // (the parent's slot in the moved buffer, its id).  The lanes of one
 // simulation reserve together; beyond the simulation's limit its own error
 // word is set (the simulation stops, the others go on).
-__device__ __noinline__ void reserve_birth(Buffers& B, Ctl* ctl, uint32_t sim, uint32_t slot, uint32_t id) {
+__device__ __noinline__ void reserve_birth(Buffers& B, Ctl* ctl, uint32_t parity, uint32_t sim, uint32_t slot,
+                                              uint32_t id) {
     cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), (int)sim);
     SimDev& S = B.sims[sim];
-    const uint32_t parity = ctl->epoch & 1u;
     uint32_t base = 0;
     if (grp.thread_rank() == 0) base = atomicAdd(&S.nbc[parity], grp.size());
     const uint32_t k = grp.shfl(base, 0) + grp.thread_rank();
@@ -285,119 +283,36 @@ __device__ __noinline__ void reserve_birth(Buffers& B, Ctl* ctl, uint32_t sim, u
 }
 
 // Phase 4: results (the histogram rank comes from the atomic between) and births.
-__device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t i, const MoveState& a,
-                                            uint32_t rank) {
+__device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t parity, uint32_t i,
+                                            const MoveState& a, uint32_t rank) {
     if (!(a.flags & 1u)) {
         B.rk[i] = kNone;
         return;
     }
     B.rk[i] = rank;  // the scatter finds the cell again from the moved record
     B.pm[cur][i] = a.p;
-    if (a.flags & 2u) reserve_birth(B, ctl, sim_of((uint32_t)a.p.w), i, a.id);
+    if (a.flags & 2u) reserve_birth(B, ctl, parity, sim_of((uint32_t)a.p.w), i, a.id);
 }
 
-
-// P5 for one entry (i proposed to j) of the last step's list: the edge is
-// final iff j's slot holds i's id and nobody proposed to i.  CONVERT changes
-// both species (-1: dies), BIND makes the carrier (the reactant with the
-// smaller D, chosen when the model was compiled) hold the other, which
-// becomes hidden.  ma / mb come in unmarked and leave as applied.
-__device__ __forceinline__ void apply_edge(Buffers& B, uint32_t cur, uint32_t i, uint32_t j, uint32_t ida,
-                                           uint32_t& ma, uint32_t& mb) {
-    const SimDev& S = B.sims[sim_of(ma)];
-    const ModelDev& Mo = B.models[S.model];
-    const uint32_t r = Mo.rx_of[ma & M_SP][mb & M_SP];
-    const ReactionDev& R = Mo.rx[r];
-    if (R.kind == 0) {  // CONVERT
-        ma = R.prod_a >= 0 ? with_species(ma, (uint32_t)R.prod_a, Mo) : ma | M_DEAD;
-        mb = R.prod_b >= 0 ? with_species(mb, (uint32_t)R.prod_b, Mo) : mb | M_DEAD;
-    } else if (R.carrier_a) {  // BIND, a carries b
-        ma |= M_BOUND | M_ROLE_A | (r << M_RXN_SHIFT);
-        B.apar[cur][i] = B.aid[cur][j];
-        mb |= M_ABSORBED;
-    } else {  // BIND, b carries a
-        mb |= M_BOUND | (r << M_RXN_SHIFT);
-        B.apar[cur][j] = ida;
-        ma |= M_ABSORBED;
-    }
-}
-
-// The whole move-pass work of one agent outside the main loop (an agent
-// whose acceptance the walk has just applied): monitor record, P1, P2, the
-// histogram rank and tile count, the moved record, births, live counts.
-template <bool kLive>
-__device__ __forceinline__ void move_one(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t epoch, uint32_t i, const int4& p,
-                                         uint32_t id) {
-    if (ctl->n_monitors) monitor_record(B, (uint32_t)p.w, kNone);
-    MoveState a;
-    a.flags = 0;
-    a.p = p;
-    a.id = id;
-    move_phase1(B, ctl, cur, i, a);
-    move_phase2(a);
-    uint32_t rank = 0;
-    if (a.flags & 1u) {
-        rank = atomicAdd(&B.cnt[a.key], 1u);
-        atomicAdd(&B.tcnt[a.key / kScanTile * kTileStride], 1u);
-        if (kLive)
-            atomicAdd((unsigned long long*)&live_buffer(B, epoch)[a.S->counts_off + count_slot((uint32_t)a.p.w, *a.Mo)],
-                      1ull);
-    }
-    a.p.w |= (int)M_WALK;  // the main loop may still read this slot: it must keep skipping it
-    move_phase4(B, ctl, cur, i, a, rank);
-}
-
-// One entry (i proposed to j) of the last step's proposal list inside the
-// move pass.  The edge is final iff nobody proposed to i (acc[i] empty) and
-// j's slot holds i's id.  The entry moves i when nobody targeted i, and j
-// when it won j's slot; every agent the list names is thus moved exactly
-// once (a targeted agent by the winner of its slot, whose edge alone decides
-// its state: its own proposal cannot be final; an untargeted proposer by its
-// own entry), and the main loop skips them.
-template <bool kLive>
-__device__ __noinline__ void walk_entry(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t epoch, uint32_t k) {
-    const uint2 e = B.props[k];
-    const uint32_t i = e.x, j = e.y;
-    const uint32_t ida = B.aid[cur][i];
-    const uint64_t ka = B.acc[i], kb = B.acc[j];
-    const bool own_i = ka == kEmpty, wins = (uint32_t)kb == ida;
-    if (!own_i && !wins) return;
-    int4 pa = B.pm[cur][i], pb = make_int4(0, 0, 0, 0);
-    uint32_t jd = 0;
-    if (wins) {
-        pb = B.pm[cur][j];
-        jd = B.aid[cur][j];
-    }
-    uint32_t ma = (uint32_t)pa.w & ~M_WALK, mb = (uint32_t)pb.w & ~M_WALK;
-    if (own_i && wins) apply_edge(B, cur, i, j, ida, ma, mb);
-    if (own_i) {
-        pa.w = (int)ma;
-        move_one<kLive>(B, ctl, cur, epoch, i, pa, ida);
-    }
-    if (wins) {
-        pb.w = (int)mb;
-        move_one<kLive>(B, ctl, cur, epoch, j, pb, jd);
-    }
-}
 
 template <bool kLive>
 __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
     const uint32_t cur = ctl->cur;
     const uint32_t n = ctl->n_buf[cur];
-    const uint32_t epoch = ctl->epoch;
+    const uint32_t epoch = ctl->epoch, parity = epoch & 1u;
     if (bid == 0 && threadIdx.x == 0) ctl->n_sorted = 0;  // the scan writes the count (if any cell is in use)
     const int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
+    // proposal slots touched last step become empty again (the list is short)
+    const uint32_t np = ctl->n_props[parity ^ 1u];
     const uint32_t stride = nb * blockDim.x;
+    for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += stride) B.acc[B.props[k].y] = kEmpty;
     // threshold monitors add up the records as they stand after t steps (a
-    // loop of its own: it keeps the main loop's register count); agents the
-    // last step's proposal list names are added by the walk below
+    // loop of its own: it keeps the main loop's register count)
     if (ctl->n_monitors)
-        for (uint32_t i = bid * blockDim.x + threadIdx.x; i < n; i += stride) {
-            const uint32_t meta = (uint32_t)pm[i].w;
-            monitor_record(B, (meta & M_WALK) ? (meta | M_DEAD) : meta, kNone);
-        }
+        for (uint32_t i = bid * blockDim.x + threadIdx.x; i < n; i += stride)
+            monitor_record(B, (uint32_t)pm[i].w, kNone);
     // Each warp takes a contiguous range of agents, 32 consecutive ones per
     // iteration (coalesced).  The next 32 records are loaded while these run
     // their chain of dependent table lookups and the histogram atomic.  The
@@ -437,15 +352,12 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
         a.flags = 0;
         a.p = nx_p;
         a.id = nx_id;
-        // M_WALK: moved by the walk below (the walk's moved record keeps the
-        // mark, so a late read here skips it too)
-        const bool mine = i < wend && !((uint32_t)a.p.w & M_WALK);
         if (i + 32 < wend) {
             nx_p = pm[i + 32];
             nx_id = aid[i + 32];
         }
-        if (mine) {
-            move_phase1(B, ctl, cur, i, a);
+        if (i < wend) {
+            move_phase1(B, ctl, cur, parity, i, a);
             move_phase2(a);
         }
         const uint32_t rank = (a.flags & 1u) ? atomicAdd(&B.cnt[a.key], 1u) : 0u;
@@ -462,7 +374,7 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
             run_n += __popc(same);
             if (tile != kNone && tile != t0) atomicAdd(&B.tcnt[tile * kTileStride], 1u);
         }
-        if (mine) move_phase4(B, ctl, cur, i, a, rank);
+        if (i < wend) move_phase4(B, ctl, cur, parity, i, a, rank);
         if (count_live && (a.flags & 1u)) {
             const uint32_t meta = (uint32_t)a.p.w, slot = count_slot(meta, *a.Mo);
             if (sim_of(meta) == s_live_sim) atomicAdd(&s_live[slot], 1u);
@@ -470,18 +382,6 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
         }
     }
     if (run_n && lane == 0) atomicAdd(&B.tcnt[run_tile * kTileStride], run_n);
-    // the last step's acceptance: warps that are done take 32 list entries
-    // at a time, so the walk fills the pass's tail
-    if (ctl->pending) {
-        const uint32_t np = ctl->n_props[(epoch & 1u) ^ 1u];
-        for (;;) {
-            uint32_t k0 = 0;
-            if (lane == 0) k0 = atomicAdd(&ctl->walk_next, 32u);
-            k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
-            if (k0 >= np) break;
-            if (k0 + lane < np) walk_entry<kLive>(B, ctl, cur, epoch, k0 + lane);
-        }
-    }
     if (count_live) {
         __syncthreads();
         if (s_live_sim != kNone) {
@@ -683,8 +583,6 @@ __device__ void bookkeeping_block(Buffers& B) {
         ctl->epoch = epoch + 1u;
         ctl->n_extra[parity ^ 1u] = 0;
         ctl->n_props[parity] = 0;
-        ctl->pending = 1;    // this step's acceptance goes to the next move pass
-        ctl->walk_next = 0;
     }
 }
 
@@ -732,10 +630,6 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
     const uint32_t nxt = ctl->cur, cur = nxt ^ 1u;
     const uint32_t epoch = ctl->epoch, parity = (epoch - 1u) & 1u;
     const uint32_t n_in = ctl->n_buf[cur], total = n_in + ctl->n_extra[parity];
-    // proposal slots claimed last step become empty again (the move pass has
-    // applied their acceptance; the list is short)
-    const uint32_t np = ctl->n_props[parity ^ 1u];
-    for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += nb * blockDim.x) B.acc[B.props[k].y] = kEmpty;
     // the scan has read this step's tile counts: zero them for the next step
     const uint32_t ntiles = (ctl->n_cells + kScanTile - 1) / kScanTile;
     for (uint32_t t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) B.tcnt[t * kTileStride] = 0;
@@ -782,8 +676,8 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
                 raise_error(ctl, ERR_CAPACITY_AGENTS, dest[u]);
                 continue;
             }
-            const uint32_t meta = (uint32_t)p[u].w & ~M_WALK;
-            B.pm[nxt][dest[u]] = make_int4(p[u].x, p[u].y, p[u].z, (int)meta);
+            const uint32_t meta = (uint32_t)p[u].w;
+            B.pm[nxt][dest[u]] = p[u];
             B.aid[nxt][dest[u]] = id[u];
             B.pflag[dest[u]] = (meta & (M_PROP | M_BOUND)) == M_PROP;
             if (meta & M_BOUND) B.apar[nxt][dest[u]] = par[u];
@@ -838,11 +732,6 @@ __device__ __forceinline__ void claim(Buffers& B, const Best& best, uint32_t ida
     atomicMin((unsigned long long*)&B.acc[best.target], (unsigned long long)((best.key & 0xFFFFFFFF00000000ull) | ida));
     const uint32_t k = reserve(&B.ctl->n_props[parity]);  // k < capacity: at most one proposal per agent
     B.props[k] = make_uint2(gi, best.target);
-    // marks for the acceptance walk (bit 30 of the meta word, which the
-    // search does not read: concurrent candidate reads are unaffected)
-    const uint32_t cur = B.ctl->cur;
-    atomicOr(reinterpret_cast<uint32_t*>(&B.pm[cur][gi]) + 3, M_WALK);
-    atomicOr(reinterpret_cast<uint32_t*>(&B.pm[cur][best.target]) + 3, M_WALK);
 }
 
 // ------------------------------------------------------------------------
@@ -980,8 +869,7 @@ __device__ __forceinline__ void place_births(Buffers& B, uint32_t cur, uint32_t 
         const ModelDev& Mo = B.models[S.model];
         int4 q = B.pm[src][seg[k].x];
         const uint32_t meta = (uint32_t)q.w;
-        q.w = (int)with_species(meta & ~(M_RXN | M_BOUND | M_ROLE_A | M_WALK), (uint32_t)Mo.sp[meta & M_SP].emit,
-                                Mo);
+        q.w = (int)with_species(meta & ~(M_RXN | M_BOUND | M_ROLE_A), (uint32_t)Mo.sp[meta & M_SP].emit, Mo);
         const uint32_t dst = ns + s_bofs[s] + rank;
         B.pm[cur][dst] = q;
         B.aid[cur][dst] = S.nid0 + rank;
@@ -1010,41 +898,49 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
 }
 
 // ------------------------------------------------------------------------
-// k_flush: the last step's acceptance applied between steps (before the host
-// reads or changes the state): every final edge, each written by its own
-// entry (final edges are disjoint), the marks cleared, the live counts
-// corrected.  The host then clears ctl.pending, so the next move pass moves
-// every agent in its main loop.
-__global__ void __launch_bounds__(kThreads) k_flush(Buffers B) {
+// k_accept: walks the proposal list; edge i -> j is final iff j's slot holds
+// i's id and nobody proposed to i.  Final edges are disjoint, so each is
+// applied without further synchronisation.
+__device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t nb) {
     Ctl* ctl = B.ctl;
-    if (ld_volatile(&ctl->err) || !ctl->pending) return;
     const uint32_t cur = ctl->cur;  // the sorted buffer
     const uint32_t epoch = ctl->epoch, parity = (epoch - 1u) & 1u;
     const uint32_t np = ctl->n_props[parity];
     uint64_t* live = ctl->live_counts ? live_buffer(B, epoch - 1u) : nullptr;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+    int4* __restrict__ pm = B.pm[cur];
+    uint32_t* __restrict__ aid = B.aid[cur];
+    uint32_t* __restrict__ apar = B.apar[cur];
+    for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += nb * blockDim.x) {
         const uint2 e = B.props[k];
         const uint32_t i = e.x, j = e.y;
-        uint32_t* wa = reinterpret_cast<uint32_t*>(&B.pm[cur][i]) + 3;
-        uint32_t* wb = reinterpret_cast<uint32_t*>(&B.pm[cur][j]) + 3;
+        // the two meta words are loaded with the slots (one round trip less)
+        uint32_t* wa = reinterpret_cast<uint32_t*>(&pm[i]) + 3;
+        uint32_t* wb = reinterpret_cast<uint32_t*>(&pm[j]) + 3;
         const uint64_t kb = B.acc[j];
-        const uint32_t ida = B.aid[cur][i];
+        const uint32_t ida = aid[i];
         const uint64_t ka = B.acc[i];
-        const bool own_i = ka == kEmpty, wins = (uint32_t)kb == ida;
-        uint32_t ma = *wa & ~M_WALK, mb = *wb & ~M_WALK;
-        // the marks go with the applied state; each marked agent has exactly
-        // one writer: a targeted one the entry that won its slot, an
-        // untargeted proposer its own entry (acc is not written here)
-        if (own_i && !wins) *wa = ma;
-        if (wins && !own_i) *wb = mb;
-        if (!own_i || !wins) continue;
+        uint32_t ma = *wa, mb = *wb;
+        if ((uint32_t)kb != ida || ka != kEmpty) continue;
         const uint32_t ma0 = ma, mb0 = mb;
-        apply_edge(B, cur, i, j, ida, ma, mb);
+        const SimDev& S = B.sims[sim_of(ma)];
+        const ModelDev& Mo = B.models[S.model];
+        const uint32_t r = Mo.rx_of[ma & M_SP][mb & M_SP];
+        const ReactionDev& R = Mo.rx[r];
+        if (R.kind == 0) {  // CONVERT
+            ma = R.prod_a >= 0 ? with_species(ma, (uint32_t)R.prod_a, Mo) : ma | M_DEAD;
+            mb = R.prod_b >= 0 ? with_species(mb, (uint32_t)R.prod_b, Mo) : mb | M_DEAD;
+        } else if (R.carrier_a) {  // BIND, a carries b
+            ma |= M_BOUND | M_ROLE_A | (r << M_RXN_SHIFT);
+            apar[i] = aid[j];
+            mb |= M_ABSORBED;
+        } else {  // BIND, b carries a
+            mb |= M_BOUND | (r << M_RXN_SHIFT);
+            apar[j] = ida;
+            ma |= M_ABSORBED;
+        }
         *wa = ma;
         *wb = mb;
         if (live) {  // the move pass counted both as they were
-            const SimDev& S = B.sims[sim_of(ma0)];
-            const ModelDev& Mo = B.models[S.model];
             unsigned long long* L = (unsigned long long*)live + S.counts_off;
             atomicAdd(L + count_slot(ma0, Mo), ~0ull);
             atomicAdd(L + count_slot(mb0, Mo), ~0ull);
@@ -1052,6 +948,13 @@ __global__ void __launch_bounds__(kThreads) k_flush(Buffers B) {
             if (!(mb & (M_DEAD | M_ABSORBED))) atomicAdd(L + count_slot(mb, Mo), 1ull);
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_accept(Buffers B) {
+    pdl_wait();
+    if (ld_volatile(&B.ctl->err)) return;
+    accept_pass(B, blockIdx.x, gridDim.x);
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------------------
@@ -1293,12 +1196,8 @@ cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool 
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_scatter, L.blocks_agents, s, B);
     if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, propose_smem(B));
+    if (e == cudaSuccess) e = launch_pdl(k_accept, L.blocks_accept, s, B);
     return e;
-}
-
-cudaError_t launch_flush(const Buffers& B, const Launch& L, cudaStream_t s) {
-    k_flush<<<L.blocks_accept, kThreads, 0, s>>>(B);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev, bool live) {
@@ -1314,7 +1213,8 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
     cudaEventRecord(ev[4], s);
     k_propose<<<L.blocks_propose, kThreads, propose_smem(B), s>>>(B);
     cudaEventRecord(ev[5], s);
-    cudaEventRecord(ev[6], s);  // the acceptance runs inside the next k_move
+    k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
+    cudaEventRecord(ev[6], s);
     return cudaGetLastError();
 }
 

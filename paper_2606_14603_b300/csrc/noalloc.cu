@@ -26,7 +26,6 @@ namespace abm {
 bool internal_view(abm_sim* s, Buffers* B, Launch* L, cudaStream_t* stream, int32_t* sim, std::string** err,
                    int* device);
 abm_status internal_cuda_fail(abm_sim* s, cudaError_t e, const char* where);
-abm_status internal_flush(abm_sim* s);
 }
 
 using namespace abm;
@@ -118,7 +117,6 @@ extern "C" abm_status abm_dump_noalloc(abm_sim* s, abm_record* out, size_t cap, 
         *err = buf;
         return ABM_EDEVICE;
     }
-    if (internal_flush(s) != ABM_OK) return ABM_ECUDA;  // the last step's acceptance, if pending
     if (!g_scratch_addr[dev]) {  // set-up, once per device, with that device current
         void* addr = nullptr;
         e = cudaGetSymbolAddress(&addr, g_dump_scratch);

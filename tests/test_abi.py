@@ -110,8 +110,6 @@ def test_batch_arena_bytes_rejects_bad_options(A):
     assert A.Batch.arena_bytes(0, 10, 1) == 0
     assert A.Batch.arena_bytes(10, 10, 0) == 0
     assert A.Batch.arena_bytes(10, 10, 5000) == 0
-    assert A.Batch.arena_bytes(10, 10, 1025) == 0          # simulation slots: 10 bits of the meta word
-    assert A.Batch.arena_bytes(10, 10, 1024) > 0
     assert A.Batch.arena_bytes(1000, 1000, 4) > 0
 
 
