@@ -308,9 +308,11 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0, cpu=True):
     sims = W.sweep(scale)
     models = [m for m, _ in sims]
     n_total = sum(m.n_agents for m in models)
-    best, tried = autotune.tune(sims, cell_deltas=(0, 1), blocks=(0,), groups=(1, 2, 4, 8), steps=10,
-                                warmup=2)
-    grp = autotune.BatchGroup(sims, best.cell_delta, best.blocks_per_sm, best.groups)
+    best, tried = autotune.tune(sims, cell_deltas=(0, 1), blocks=(0, 3, 2), groups=(2, 1, 4, 8),
+                                threads=(256, 128, 512), chunks=(0, 1024, 2048, 4096), steps=10, warmup=2,
+                                search="axes")
+    grp = autotune.BatchGroup(sims, best.cell_delta, best.blocks_per_sm, best.groups,
+                              threads_per_block=best.threads_per_block, propose_chunk=best.propose_chunk)
     grp.step(warmup)
     grp.sync()
     torch.cuda.synchronize()
@@ -335,9 +337,12 @@ def run_sweep(A, torch, stream, steps, warmup=5, scale=1.0, cpu=True):
     cpu_line = sweep_cpu_baseline(scale=scale) if cpu else None
     return {"cpu_baseline": cpu_line, "sims": len(sims), "agents": n_total, "live_after": live, "steps": steps,
             "autotune": {"cell_delta": best.cell_delta, "blocks_per_sm": best.blocks_per_sm,
-                         "groups": best.groups,
-                         "candidates": [[c.cell_delta, c.blocks_per_sm, c.groups, round(c.ms_per_step, 4)]
-                                        for c in tried]},
+                         "groups": best.groups, "threads_per_block": best.threads_per_block,
+                         "propose_chunk": best.propose_chunk, "search": "axis by axis",
+                         "candidates": [[c.cell_delta, c.blocks_per_sm, c.groups, c.threads_per_block,
+                                         c.propose_chunk, round(c.ms_per_step, 4)] for c in tried],
+                         "candidate_fields": ["cell_delta", "blocks_per_sm", "groups", "threads_per_block",
+                                              "propose_chunk", "ms_per_step"]},
             "batched_value": batched, "serial_value": serial, "unit": UNIT,
             "batched_over_serial": batched / serial, "batched_ms_per_step": batched_ms / steps,
             "serial_ms_per_round": serial_ms / steps}

@@ -135,9 +135,17 @@ typedef struct {
     size_t         arena_bytes;
     void*          stream;
     const int16_t* ncdf_table;
-    uint32_t       blocks_per_sm;    /* CTAs of 256 threads per SM for the move and
-                                        scatter kernels (grid-stride); 0 = as many
-                                        as fit on an SM at once */
+    uint32_t       blocks_per_sm;    /* CTAs per SM for the move and scatter
+                                        kernels (grid-stride); 0 = as many as fit
+                                        on an SM at once */
+    /* Launch shape (an autotuner's knobs; no choice changes a result): */
+    uint32_t       threads_per_block;/* block size of the move and scatter
+                                        kernels: 128, 256 or 512; 0 = 256    */
+    uint32_t       propose_chunk;    /* sorted agents per block of the
+                                        proximity search (a block covers
+                                        several small simulations or part of a
+                                        large one): 1024, 2048 or 4096;
+                                        0 = by capacity                      */
 } abm_batch_options;
 
 /* Layout of abm_*_counts output (uint64 each):

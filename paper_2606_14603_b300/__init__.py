@@ -67,7 +67,8 @@ class BatchOptions(C.Structure):
     _fields_ = [("capacity_agents", C.c_uint64), ("capacity_cells", C.c_uint64),
                 ("max_sims", C.c_uint32), ("births_per_step", C.c_uint32), ("arena", C.c_void_p),
                 ("arena_bytes", C.c_size_t), ("stream", C.c_void_p), ("ncdf_table", C.c_void_p),
-                ("blocks_per_sm", C.c_uint32)]
+                ("blocks_per_sm", C.c_uint32), ("threads_per_block", C.c_uint32),
+                ("propose_chunk", C.c_uint32)]
 
 
 class Monitor(C.Structure):
@@ -403,14 +404,15 @@ class Batch:
     tables on the device).  Simulations may be added and removed between steps."""
 
     def __init__(self, capacity_agents: int, capacity_cells: int, max_sims: int,
-                 births_per_step: int = 0, arena=None, stream=None, blocks_per_sm: int = 0):
+                 births_per_step: int = 0, arena=None, stream=None, blocks_per_sm: int = 0,
+                 threads_per_block: int = 0, propose_chunk: int = 0):
         L = lib()
         aptr, abytes = (None, 0)
         if arena is not None:
             aptr, abytes = arena.data_ptr(), arena.numel() * arena.element_size()
         self._arena = arena
         o = BatchOptions(capacity_agents, capacity_cells, max_sims, births_per_step, aptr, abytes,
-                         _stream_ptr(stream), None, blocks_per_sm)
+                         _stream_ptr(stream), None, blocks_per_sm, threads_per_block, propose_chunk)
         h = C.c_void_p()
         st = L.abm_batch_create(C.byref(o), C.byref(h))
         if st != OK:
@@ -421,7 +423,7 @@ class Batch:
 
     @staticmethod
     def arena_bytes(capacity_agents: int, capacity_cells: int, max_sims: int, births_per_step: int = 0) -> int:
-        o = BatchOptions(capacity_agents, capacity_cells, max_sims, births_per_step, None, 0, None, None, 0)
+        o = BatchOptions(capacity_agents, capacity_cells, max_sims, births_per_step, None, 0, None, None, 0, 0, 0)
         return lib().abm_batch_arena_bytes(C.byref(o))
 
     def add(self, model, seed: int, cell_log2: int = 0) -> int:

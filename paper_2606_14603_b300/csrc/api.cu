@@ -557,6 +557,9 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
         return ABM_EINVAL;
     if (o->capacity_agents >= 0x7FFFFFFFull || o->capacity_cells >= 0xFFFFF000ull) return ABM_EINVAL;
     if (o->blocks_per_sm > 64) return ABM_EINVAL;
+    if (o->threads_per_block && !valid_move_threads((int)o->threads_per_block)) return ABM_EINVAL;
+    if (o->propose_chunk && o->propose_chunk != 1024 && o->propose_chunk != 2048 && o->propose_chunk != 4096)
+        return ABM_EINVAL;
     const uint32_t births = births_quota(o->births_per_step, o->capacity_agents);
     std::string msg;
     abm_status st = check_device(&msg);
@@ -659,10 +662,18 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     // once (a grid-stride loop, no tail wave); the proposal search with one
     // chunk of sorted agents per CTA, so that the hardware balances chunks of
     // unequal work, and chunks large enough to amortise their compaction
-    const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm();
-    b->L.blocks_agents = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * per_sm));
+    b->L.blocks_agents =
+        (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * (uint64_t)move_blocks_per_sm(256)));
+    // the move and scatter passes: block size and CTAs per SM from the options
+    // (the autotuner's knobs), else 256 threads and as many CTAs as fit
+    const int tm = o->threads_per_block ? (int)o->threads_per_block : 256;
+    const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm(tm);
+    b->L.threads_move = tm;
+    b->L.blocks_move = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((b->cap_agents + tm - 1) / tm, (uint64_t)sms * per_sm));
     uint64_t chunk = 1024;
     while (chunk < 4096 && chunk * (uint64_t)sms * 8 < b->cap_agents) chunk *= 2;
+    if (o->propose_chunk) chunk = o->propose_chunk;
     B.propose_chunk = (uint32_t)chunk;
     b->L.blocks_propose =
         (int)std::max<uint64_t>(1, std::min<uint64_t>((b->cap_agents + chunk - 1) / chunk, (uint64_t)sms * 32));

@@ -305,7 +305,9 @@ __device__ __forceinline__ bool mon_due(const MonDev& M, uint32_t t) {
 // ------------------------------------------------------------------------
 // Host-side launch wrappers (kernels.cu).
 struct Launch {
-    int blocks_agents;       // grid of the per-agent kernels (grid-stride)
+    int blocks_agents;       // grid of the between-step per-agent kernels (grid-stride, 256 threads)
+    int blocks_move;         // grid of k_move and k_scatter: the blocks of threads_move that fit at once
+    int threads_move;        // block size of k_move and k_scatter: 128, 256 or 512
     int threads;             // 256
     int blocks_scan;
     int blocks_accept;       // CTAs of the acceptance kernel (walks the proposal list)
@@ -313,8 +315,10 @@ struct Launch {
     bool prefix_kernel;      // more than kDirectTiles tiles: tile prefixes by k_tile_prefix
 };
 
-// CTAs of k_move that fit on one SM at once (its registers decide).
-int move_blocks_per_sm();
+// CTAs of k_move with `threads` threads that fit on one SM at once (its
+// registers decide); valid block sizes are 128, 256 and 512.
+int move_blocks_per_sm(int threads);
+bool valid_move_threads(int threads);
 size_t propose_smem(const Buffers& B);
 
 cudaError_t prepare_kernels();

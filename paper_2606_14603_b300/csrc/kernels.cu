@@ -392,8 +392,10 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     }
 }
 
-template <bool kLive>
-__global__ void __launch_bounds__(kThreads, 4) k_move(Buffers B) {
+// Block size TB (128, 256 or 512 threads; the autotuner's choice) with the
+// register budget of 64 per thread either way.
+template <bool kLive, int TB>
+__global__ void __launch_bounds__(TB, 1024 / TB) k_move(Buffers B) {
     pdl_wait();
     if (ld_volatile(&B.ctl->err)) return;
     move_pass<kLive>(B, blockIdx.x, gridDim.x);
@@ -685,7 +687,8 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_scatter(Buffers B) {
+template <int TB>
+__global__ void __launch_bounds__(TB) k_scatter(Buffers B) {
     pdl_wait();
     if (ld_volatile(&B.ctl->err)) return;
     scatter_pass(B, blockIdx.x, gridDim.x);
@@ -1184,32 +1187,50 @@ cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B
 // births prefix of every simulation slot.
 size_t propose_smem(const Buffers& B) { return 4 * ((size_t)B.propose_chunk + B.max_sims + 1); }
 
-int move_blocks_per_sm() {
+namespace {
+using StepKernel = void (*)(Buffers);
+// k_move (without, with live counts) and k_scatter for a block size
+struct MoveKernels {
+    StepKernel move, move_live, scatter;
+};
+MoveKernels move_kernels(int threads) {
+    if (threads == 128) return {k_move<false, 128>, k_move<true, 128>, k_scatter<128>};
+    if (threads == 512) return {k_move<false, 512>, k_move<true, 512>, k_scatter<512>};
+    return {k_move<false, 256>, k_move<true, 256>, k_scatter<256>};
+}
+}  // namespace
+
+bool valid_move_threads(int threads) { return threads == 128 || threads == 256 || threads == 512; }
+
+int move_blocks_per_sm(int threads) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<false>, kThreads, 0) != cudaSuccess || n < 1) n = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, move_kernels(threads).move, threads, 0) != cudaSuccess ||
+        n < 1)
+        n = 1024 / threads;
     return n;
 }
 
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool live) {
-    cudaError_t e = launch_pdl(live ? k_move<true> : k_move<false>, L.blocks_agents, s, B);
+    const MoveKernels mk = move_kernels(L.threads_move);
+    cudaError_t e = launch_pdl(live ? mk.move_live : mk.move, L.blocks_move, s, B, 0, L.threads_move);
     if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1, s, B);
-    if (e == cudaSuccess) e = launch_pdl(k_scatter, L.blocks_agents, s, B);
+    if (e == cudaSuccess) e = launch_pdl(mk.scatter, L.blocks_move, s, B, 0, L.threads_move);
     if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, propose_smem(B));
     if (e == cudaSuccess) e = launch_pdl(k_accept, L.blocks_accept, s, B);
     return e;
 }
 
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev, bool live) {
+    const MoveKernels mk = move_kernels(L.threads_move);
     cudaEventRecord(ev[0], s);
-    if (live) k_move<true><<<L.blocks_agents, kThreads, 0, s>>>(B);
-    else k_move<false><<<L.blocks_agents, kThreads, 0, s>>>(B);
+    (live ? mk.move_live : mk.move)<<<L.blocks_move, L.threads_move, 0, s>>>(B);
     cudaEventRecord(ev[1], s);
     if (L.prefix_kernel) k_tile_prefix<<<1, 1024, 0, s>>>(B);
     cudaEventRecord(ev[2], s);
     k_scan<<<L.blocks_scan + 1, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[3], s);
-    k_scatter<<<L.blocks_agents, kThreads, 0, s>>>(B);
+    mk.scatter<<<L.blocks_move, L.threads_move, 0, s>>>(B);
     cudaEventRecord(ev[4], s);
     k_propose<<<L.blocks_propose, kThreads, propose_smem(B), s>>>(B);
     cudaEventRecord(ev[5], s);
