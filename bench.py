@@ -171,16 +171,16 @@ def launches_per_step(cells):
 
 
 def ncu_traffic(kernel):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
-    kernel sources (kernels.cu + engine.cuh) are unchanged since the capture
-    (else None)."""
+    """DRAM bytes (read + write) per 1M-agent launch of a kernel from the
+    committed ncu summary, if the kernel sources (kernels.cu + engine.cuh) are
+    unchanged since the capture (else None): (bytes, units, unit, note)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         sha = kernel_source_sha()
         for line in open(path):
-            f = line.split()
+            f = line.split(None, 5)
             if len(f) >= 5 and not line.startswith("#") and f[0] == kernel and f[1] == sha:
-                return float(f[2]), float(f[3]), f[4]
+                return float(f[2]), float(f[3]), f[4], (f[5].strip() if len(f) > 5 else "")
     except OSError:
         pass
     return None
@@ -494,12 +494,20 @@ def main():
     dom_ms = prof[dom] / P
     achieved = bpu * units / (dom_ms / 1e3) / 1e9
     traffic = ncu_traffic(dom)
+    # the dominant kernel's time inside the graphed step (launches overlap through
+    # programmatic dependent launch there): its share of the event-timed kernels
+    # times the graphed step time
     step_ms_avg = total_ms / K
+    dom_ms_graph = share[dom] * step_ms_avg
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic[0] if traffic else None,
             "bytes_per_unit": bpu, "units_per_launch": units, "unit_of_work": unit_name,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.4 TB/s",
-            "kernel_ms": dom_ms}
+            "kernel_ms": dom_ms,
+            "kernel_ms_is": "CUDA events around the kernel, step launched without the graph (frac uses this)",
+            "kernel_ms_graph_est": dom_ms_graph,
+            "frac_graph_est": bpu * units / (dom_ms_graph / 1e3) / 1e9 / hbm,
+            "traffic_source": (f"ncu {traffic[3]}" if traffic and len(traffic) > 3 else None)}
     step_roof = {"bytes_per_molecule_step": STEP_BYTES_PER_AGENT,
                  "achieved_gbs": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9,
                  "frac": STEP_BYTES_PER_AGENT * n_agents / (step_ms_avg / 1e3) / 1e9 / hbm}
