@@ -818,8 +818,16 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
                 ra[r] = in ? start[row + xlo] : 0u;
                 rb[r] = in ? start[row + xhi + 1] : 0u;
             }
-#pragma unroll
-            for (int r = 0; r < 4; r++) walk(ra[r], rb[r]);
+            // the four ranges walked as one sequence of candidates (the same
+            // order), so that a warp waits for its longest total, not for the
+            // longest range of each row in turn
+            const uint32_t e0 = rb[0] - ra[0], e1 = e0 + rb[1] - ra[1], e2 = e1 + rb[2] - ra[2];
+            const uint32_t total = e2 + rb[3] - ra[3];
+            for (uint32_t t = 0; t < total; t++) {
+                const uint32_t j = t < e0 ? ra[0] + t : t < e1 ? ra[1] + (t - e0) : t < e2 ? ra[2] + (t - e1)
+                                                                                          : ra[3] + (t - e2);
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.tau, best);
+            }
         } else {
             // a box wider than half a cell can meet 3 cells per axis (a cell is
             // never smaller than a contact radius): up to 3 x 3 rows
