@@ -823,10 +823,20 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
             // longest range of each row in turn
             const uint32_t e0 = rb[0] - ra[0], e1 = e0 + rb[1] - ra[1], e2 = e1 + rb[2] - ra[2];
             const uint32_t total = e2 + rb[3] - ra[3];
+            auto cand = [&](uint32_t t) -> uint32_t {
+                return t < e0 ? ra[0] + t : t < e1 ? ra[1] + (t - e0) : t < e2 ? ra[2] + (t - e1) : ra[3] + (t - e2);
+            };
+            // the next candidate's record is requested while this one is examined
+            uint32_t jn = total ? cand(0) : 0u;
+            int4 qn = total ? pm[jn] : make_int4(0, 0, 0, 0);
             for (uint32_t t = 0; t < total; t++) {
-                const uint32_t j = t < e0 ? ra[0] + t : t < e1 ? ra[1] + (t - e0) : t < e2 ? ra[2] + (t - e1)
-                                                                                          : ra[3] + (t - e2);
-                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.tau, best);
+                const uint32_t j = jn;
+                const int4 q = qn;
+                if (t + 1 < total) {
+                    jn = cand(t + 1);
+                    qn = pm[jn];
+                }
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q, j, aid, S.tau, best);
             }
         } else {
             // a box wider than half a cell can meet 3 cells per axis (a cell is
