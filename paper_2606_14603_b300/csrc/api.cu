@@ -250,7 +250,7 @@ uint32_t births_quota(uint64_t want, uint64_t cap_agents) {
 }
 
 struct Layout {
-    size_t off[32];
+    size_t off[48];
     size_t total;
 };
 
@@ -265,6 +265,7 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
         4 * C, 8 * C, 8 * C, (size_t)C,        // rk, acc, props, pflag
         16 * E, 4 * E, 4 * E,                  // extras
         8 * (size_t)Bc * S, 4 * ((size_t)S + 1),  // births: one segment per simulation slot, prefixes
+        4 * (size_t)Bc * S, 4 * ((size_t)S + 1),  // sorted tiles of long births segments, their prefixes
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
         4 * kTileStride * tiles,               // tile counts (one per 128-byte line)
         4 * tiles,                             // tile prefixes
@@ -279,7 +280,8 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
     };
     Layout L{};
     size_t o = 0;
-    const int n = (int)(sizeof(sizes) / sizeof(sizes[0]));
+    constexpr int n = (int)(sizeof(sizes) / sizeof(sizes[0]));
+    static_assert(n < (int)(sizeof(L.off) / sizeof(L.off[0])), "layout table too small");
     for (int i = 0; i < n; i++) {
         L.off[i] = o;
         o += align_up(sizes[i]);
@@ -624,6 +626,8 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.xrk = (uint32_t*)at();
     B.bseg = (uint2*)at();
     B.bofs = (uint32_t*)at();
+    B.bsrt = (uint32_t*)at();
+    B.btofs = (uint32_t*)at();
     B.cnt = (uint32_t*)at();
     B.start = (uint32_t*)at();
     B.tcnt = (uint32_t*)at();

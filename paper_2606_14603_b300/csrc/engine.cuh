@@ -13,6 +13,9 @@
 //   bseg[S][Q]   births of the step, one segment of Q per simulation slot:
 //                (parent's slot in the moved buffer, parent id)
 //   bofs[S+1]    births placed before each simulation this step (prefix)
+//   bsrt[S][Q]   parent ids of a long births segment, sorted tile by tile
+//                (kBirthTile entries each), for the ranking by binary search
+//   btofs[S+1]   sorted tiles before each simulation this step (prefix)
 //   cnt[K], start[K+1]  per-cell histogram and its exclusive scan
 //   tcnt[T]      agents per cell tile (8192 cells), counted by the move pass,
 //                one counter per 128-byte line (kTileStride words apart) so
@@ -41,6 +44,8 @@ constexpr int kMaxReactions = 255;
 constexpr int kMaxComp = 4;
 constexpr int kMaxSims = 2048;
 constexpr uint32_t kDefaultBirths = 8192;   // default births per step of one simulation
+constexpr uint32_t kBirthTile = 2048;       // births segments longer than this are ranked through sorted tiles
+constexpr uint32_t kSortBlocks = 16;        // blocks of k_scan that sort those tiles
 constexpr int kScanTile = 8192;           // cells per scan tile (256 threads x 32)
 constexpr int kTileStride = 32;           // words between two tile counters
 constexpr uint32_t kDirectTiles = 8192;   // up to this many tiles, each scan block adds up its own prefix
@@ -125,6 +130,8 @@ struct SimDev {              // per simulation slot
     uint32_t nid0;           // id of the step's first child (next_id before the step's births)
     uint32_t err;            // per-simulation error (SIM_ERR_*), sticky; the simulation is frozen
     uint32_t err_info;
+    uint32_t nbt;            // sorted tiles of this step's births (0: ranked by direct comparison)
+    uint32_t pad_sim;
 };
 
 // Threshold monitor of one simulation slot (Sec. 2: designated species
@@ -159,7 +166,8 @@ struct Ctl {
     uint32_t live_counts;    // 1: each step leaves the counts of its result in live[epoch & 1]
     uint32_t n_compact;      // agents kept by a compaction (between steps)
     uint32_t sim_errs;       // simulations that raised a per-simulation error
-    uint32_t pad[3];
+    uint32_t move_parity;    // epoch & 1 of the step in flight, written by its move pass
+    uint32_t pad[2];
 };
 
 struct Buffers {
@@ -175,6 +183,8 @@ struct Buffers {
     uint32_t* xrk;
     uint2* bseg;             // [max sims][bquota] births: (parent slot, parent id)
     uint32_t* bofs;          // [max sims + 1] births before each simulation this step
+    uint32_t* bsrt;          // [max sims][bquota] parent ids of long segments, sorted per tile
+    uint32_t* btofs;         // [max sims + 1] sorted births tiles before each simulation
     uint32_t* cnt;
     uint32_t* start;
     uint32_t* tcnt;

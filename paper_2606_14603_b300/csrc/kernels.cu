@@ -301,7 +301,10 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     const uint32_t cur = ctl->cur;
     const uint32_t n = ctl->n_buf[cur];
     const uint32_t epoch = ctl->epoch, parity = epoch & 1u;
-    if (bid == 0 && threadIdx.x == 0) ctl->n_sorted = 0;  // the scan writes the count (if any cell is in use)
+    if (bid == 0 && threadIdx.x == 0) {
+        ctl->n_sorted = 0;             // the scan writes the count (if any cell is in use)
+        ctl->move_parity = epoch & 1u;  // stable during k_scan, whose bookkeeping advances epoch
+    }
     const int4* __restrict__ pm = B.pm[cur];
     const uint32_t* __restrict__ aid = B.aid[cur];
     // proposal slots touched last step become empty again (the list is short)
@@ -553,6 +556,13 @@ __device__ void bookkeeping_block(Buffers& B) {
     }
     uint32_t total;
     uint32_t pre = block_exclusive_scan(mine, s_warp, &total);
+    // a segment longer than one tile is ranked through its sorted tiles
+    auto tiles_of = [](uint32_t n) { return n > kBirthTile ? (n + kBirthTile - 1) / kBirthTile : 0u; };
+    uint32_t tmine = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; k++) tmine += tiles_of(nb[k]);
+    uint32_t ttotal;
+    uint32_t tpre = block_exclusive_scan(tmine, s_warp, &ttotal);
 #pragma unroll
     for (uint32_t k = 0; k < kPer; k++) {
         const uint32_t s = s0 + k;
@@ -560,6 +570,9 @@ __device__ void bookkeeping_block(Buffers& B) {
         SimDev& S = B.sims[s];
         B.bofs[s] = pre;
         pre += nb[k];
+        B.btofs[s] = tpre;
+        tpre += tiles_of(nb[k]);
+        S.nbt = tiles_of(nb[k]);
         S.nbc[parity ^ 1u] = 0;
         if (!S.active) {
             S.adv = 0;
@@ -580,6 +593,7 @@ __device__ void bookkeeping_block(Buffers& B) {
     }
     if (threadIdx.x == 0) {
         B.bofs[n_sims] = total;
+        B.btofs[n_sims] = ttotal;
         ctl->nb_total = total;
         ctl->cur ^= 1u;
         ctl->epoch = epoch + 1u;
@@ -588,18 +602,82 @@ __device__ void bookkeeping_block(Buffers& B) {
     }
 }
 
+// Sorter block j of kSortBlocks in k_scan: every births segment longer than
+// kBirthTile is cut into tiles of kBirthTile births (the layout the
+// bookkeeping block also derives, for the ranking in k_propose); this block
+// sorts tiles j, j + kSortBlocks, ... : the parent ids of the tile ascending
+// in shared memory (bitonic network; a short last tile padded with the
+// largest id, which no parent has), written to bsrt at the same positions.
+// Without a long segment it finds no tile and returns.
+__device__ void sorter_block(Buffers& B, uint32_t j, uint32_t* s_keys, uint32_t* s_warp, uint32_t* s_own) {
+    Ctl* ctl = B.ctl;
+    const uint32_t parity = ctl->move_parity, n_sims = ctl->n_sims;
+    constexpr uint32_t kPer = (kMaxSims + kThreads - 1) / kThreads;
+    const uint32_t s0 = threadIdx.x * kPer;
+    uint32_t tiles[kPer], mine = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; k++) {
+        const uint32_t s = s0 + k;
+        uint32_t nb = 0;
+        if (s < n_sims && B.sims[s].active) nb = min(B.sims[s].nbc[parity], B.bquota);
+        tiles[k] = nb > kBirthTile ? (nb + kBirthTile - 1) / kBirthTile : 0u;
+        mine += tiles[k];
+    }
+    uint32_t total;
+    const uint32_t pre = block_exclusive_scan(mine, s_warp, &total);
+    for (uint32_t t = j; t < total; t += kSortBlocks) {
+        uint32_t run = pre;
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; k++) {  // the thread that owns tile t's simulation names it
+            if (t >= run && t < run + tiles[k]) {
+                s_own[0] = s0 + k;
+                s_own[1] = t - run;
+            }
+            run += tiles[k];
+        }
+        __syncthreads();
+        const uint32_t s = s_own[0], base = s_own[1] * kBirthTile;
+        const uint32_t len = min(kBirthTile, min(B.sims[s].nbc[parity], B.bquota) - base);
+        const uint2* seg = B.bseg + (size_t)s * B.bquota + base;
+        for (uint32_t k = threadIdx.x; k < kBirthTile; k += blockDim.x) s_keys[k] = k < len ? seg[k].y : kNone;
+        __syncthreads();
+        for (uint32_t size = 2; size <= kBirthTile; size <<= 1)
+            for (uint32_t stride = size / 2; stride > 0; stride >>= 1) {
+                for (uint32_t i = threadIdx.x; i < kBirthTile / 2; i += blockDim.x) {
+                    const uint32_t lo = 2 * stride * (i / stride) + i % stride, hi = lo + stride;
+                    const uint32_t a = s_keys[lo], b = s_keys[hi];
+                    if ((a > b) == ((lo & size) == 0)) {
+                        s_keys[lo] = b;
+                        s_keys[hi] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        uint32_t* out = B.bsrt + (size_t)s * B.bquota + base;
+        for (uint32_t k = threadIdx.x; k < len; k += blockDim.x) out[k] = s_keys[k];
+        __syncthreads();  // s_keys and s_own are reused by the next tile
+    }
+}
+
 // k_scan: block b scans a contiguous range of tiles; the agents before the
 // range come from the tile counts (or from k_tile_prefix on large grids).
 // The block with the last tile writes the total and the sorted-agent count.
-// The last block of the grid does the step's bookkeeping instead.
+// The block after the scan blocks does the step's bookkeeping, the
+// kSortBlocks after it sort the tiles of long births segments.
 __global__ void __launch_bounds__(kThreads) k_scan(Buffers B) {
     __shared__ uint32_t s_warp[kThreads / 32];
     Ctl* ctl = B.ctl;
     pdl_wait();
     if (ld_volatile(&ctl->err)) return;
-    const uint32_t nblk = gridDim.x - 1;
-    if (blockIdx.x == nblk) {
-        bookkeeping_block(B);
+    const uint32_t nblk = gridDim.x - 1 - kSortBlocks;
+    if (blockIdx.x >= nblk) {
+        if (blockIdx.x == nblk) {
+            bookkeeping_block(B);
+        } else {
+            __shared__ uint32_t s_keys[kBirthTile];
+            __shared__ uint32_t s_own[2];
+            sorter_block(B, blockIdx.x - nblk - 1, s_keys, s_warp, s_own);
+        }
         pdl_trigger();
         return;
     }
@@ -685,6 +763,17 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
             if (meta & M_BOUND) B.apar[nxt][dest[u]] = par[u];
         }
     }
+}
+
+// Last simulation s of [0, n) with ofs[s] <= v (ofs ascending, ofs[0] = 0 <= v).
+__device__ __forceinline__ uint32_t last_at_most(const uint32_t* ofs, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (ofs[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 template <int TB>
@@ -852,6 +941,17 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
     __syncthreads();  // s_list and s_n are reused by the next chunk
 }
 
+// Number of entries below x in the sorted keys[0, n) (binary search).
+__device__ __forceinline__ uint32_t count_below(const uint32_t* keys, uint32_t n, uint32_t x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (keys[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Births of this step (P6): each simulation's children, from its segment of
 // the births buffer, get ids nid0 + rank, the rank ordering them by parent
 // id (unique: at most one child per parent per step), and are appended
@@ -860,32 +960,57 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
 // parent's emitted species; it first acts at the next step.  Thread g of
 // the grid places the g-th birth of the step; the simulation it belongs to
 // comes from the births prefix (bofs, written by the bookkeeping block),
-// searched in shared memory.
-__device__ __forceinline__ void place_births(Buffers& B, uint32_t cur, uint32_t nbt, uint32_t ns,
-                                             uint32_t* s_bofs) {
+// searched in shared memory.  The rank: in a segment of at most kBirthTile
+// births, by comparing with every other birth of the segment; in a longer
+// one, as the sum over its tiles (sorted by the scatter) of the parent ids
+// below this one, by binary search -- the tiles staged in shared memory
+// when the block's threads share the simulation (the usual case: a long
+// segment fills whole blocks), else searched in global memory.
+__device__ __noinline__ void place_births(Buffers& B, uint32_t cur, uint32_t nbt, uint32_t ns,
+                                             uint32_t* s_bofs, uint32_t* s_tile) {
     Ctl* ctl = B.ctl;
     const uint32_t n_sims = ctl->n_sims;
     for (uint32_t s = threadIdx.x; s <= n_sims; s += blockDim.x) s_bofs[s] = B.bofs[s];
     __syncthreads();
     const uint32_t src = cur ^ 1u;  // the moved (unsorted) buffer holds the parents' records
     uint64_t* live = ctl->live_counts ? live_buffer(B, ctl->epoch - 1u) : nullptr;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nbt; g += gridDim.x * blockDim.x) {
-        uint32_t lo = 0, hi = n_sims;  // last s with s_bofs[s] <= g
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) / 2;
-            if (s_bofs[mid] <= g) lo = mid;
-            else hi = mid;
-        }
-        const uint32_t s = lo, k = g - s_bofs[s], nb = s_bofs[s + 1] - s_bofs[s];
-        const uint2* seg = B.bseg + (size_t)s * B.bquota;
-        const uint32_t pid = seg[k].y;
+    for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < nbt; g0 += gridDim.x * blockDim.x) {  // block-uniform
+        const uint32_t g = g0 + threadIdx.x;
+        const bool valid = g < nbt;
+        const uint32_t s = valid ? last_at_most(s_bofs, n_sims, g) : kNone;
+        const uint32_t s_blk = last_at_most(s_bofs, n_sims, g0);  // the block's first birth's
+        const uint32_t k = valid ? g - s_bofs[s] : 0u;
+        const uint2* seg = valid ? B.bseg + (size_t)s * B.bquota : nullptr;
+        const uint32_t pid = valid ? seg[k].y : 0u;
         uint32_t rank = 0;
-        const uint4* seg4 = reinterpret_cast<const uint4*>(seg);  // bquota is even: 16-byte aligned
-        for (uint32_t j = 0; j < nb / 2; j++) {
-            const uint4 v = seg4[j];
-            rank += (v.y < pid) + (v.w < pid);
+        // long segment of the block's simulation: its sorted tiles through shared memory
+        const uint32_t tiles_blk = B.sims[s_blk].nbt, nb_blk = s_bofs[s_blk + 1] - s_bofs[s_blk];
+        for (uint32_t t = 0; t < tiles_blk; t++) {
+            const uint32_t base = t * kBirthTile, len = min(kBirthTile, nb_blk - base);
+            const uint32_t* tile = B.bsrt + (size_t)s_blk * B.bquota + base;
+            for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) s_tile[q] = tile[q];
+            __syncthreads();
+            if (s == s_blk) rank += count_below(s_tile, len, pid);
+            __syncthreads();
         }
-        if (nb & 1u) rank += seg[nb - 1].y < pid;
+        if (!valid) continue;
+        const uint32_t nb = s_bofs[s + 1] - s_bofs[s];
+        const uint32_t tiles = B.sims[s].nbt;
+        if (tiles == 0) {
+            rank = 0;
+            const uint4* seg4 = reinterpret_cast<const uint4*>(seg);  // bquota is even: 16-byte aligned
+            for (uint32_t j = 0; j < nb / 2; j++) {
+                const uint4 v = seg4[j];
+                rank += (v.y < pid) + (v.w < pid);
+            }
+            if (nb & 1u) rank += seg[nb - 1].y < pid;
+        } else if (s != s_blk) {  // (a long segment starting inside this block)
+            rank = 0;
+            for (uint32_t t = 0; t < tiles; t++) {
+                const uint32_t base = t * kBirthTile;
+                rank += count_below(B.bsrt + (size_t)s * B.bquota + base, min(kBirthTile, nb - base), pid);
+            }
+        }
         const SimDev& S = B.sims[s];
         const ModelDev& Mo = B.models[S.model];
         int4 q = B.pm[src][seg[k].x];
@@ -899,7 +1024,7 @@ __device__ __forceinline__ void place_births(Buffers& B, uint32_t cur, uint32_t 
 }
 
 __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
-    extern __shared__ uint32_t s_list[];  // B.propose_chunk entries, then max sims + 1 birth offsets
+    extern __shared__ uint32_t s_list[];  // B.propose_chunk entries, max sims + 1 birth offsets, a births tile
     __shared__ uint32_t s_n[1 + kThreads / 32];  // scratch of the compaction's block scan
     pdl_wait();
     Ctl* ctl = B.ctl;
@@ -914,7 +1039,7 @@ __global__ void __launch_bounds__(kThreads) k_propose(Buffers B) {
     const uint32_t chunk = B.propose_chunk;
     for (uint32_t base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk)
         propose_chunk(B, base, n, parity, s_list, s_n);
-    if (nbt && fits) place_births(B, cur, nbt, n, s_list + chunk);
+    if (nbt && fits) place_births(B, cur, nbt, n, s_list + chunk, s_list + chunk + B.max_sims + 1);
     pdl_trigger();
 }
 
@@ -1201,9 +1326,9 @@ cudaError_t launch_pdl(Kernel kernel, int grid, cudaStream_t s, const Buffers& B
     return cudaLaunchKernelEx(&cfg, kernel, B);
 }
 
-// Dynamic shared memory of k_propose: the chunk's proposer list, then the
-// births prefix of every simulation slot.
-size_t propose_smem(const Buffers& B) { return 4 * ((size_t)B.propose_chunk + B.max_sims + 1); }
+// Dynamic shared memory of k_propose: the chunk's proposer list, the births
+// prefix of every simulation slot, then one sorted births tile.
+size_t propose_smem(const Buffers& B) { return 4 * ((size_t)B.propose_chunk + B.max_sims + 1 + kBirthTile); }
 
 namespace {
 using StepKernel = void (*)(Buffers);
@@ -1232,7 +1357,7 @@ cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool 
     const MoveKernels mk = move_kernels(L.threads_move);
     cudaError_t e = launch_pdl(live ? mk.move_live : mk.move, L.blocks_move, s, B, 0, L.threads_move);
     if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
-    if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1, s, B);
+    if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1 + kSortBlocks, s, B);
     if (e == cudaSuccess) e = launch_pdl(mk.scatter, L.blocks_move, s, B, 0, L.threads_move);
     if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, propose_smem(B));
     if (e == cudaSuccess) e = launch_pdl(k_accept, L.blocks_accept, s, B);
@@ -1246,7 +1371,7 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
     cudaEventRecord(ev[1], s);
     if (L.prefix_kernel) k_tile_prefix<<<1, 1024, 0, s>>>(B);
     cudaEventRecord(ev[2], s);
-    k_scan<<<L.blocks_scan + 1, kThreads, 0, s>>>(B);
+    k_scan<<<L.blocks_scan + 1 + kSortBlocks, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[3], s);
     mk.scatter<<<L.blocks_move, L.threads_move, 0, s>>>(B);
     cudaEventRecord(ev[4], s);
