@@ -13,11 +13,13 @@
 //               than 8192 tiles only)
 //   k_scan      exclusive scan of the cell histogram, tile prefixes included;
 //               one extra block does the step's bookkeeping meanwhile (births
-//               per simulation, monitors, step counters, buffer flip)
+//               per simulation, monitors, step counters, buffer flip), and
+//               16 more sort the tiles of long births segments by parent id
 //   k_scatter   reorder every live agent by cell into the other buffer
 //   k_propose   neighbour query over the cells a contact radius can reach,
 //               nearest eligible partner, atomicMin on a packed key; births
-//               ranked by parent id and placed after the sorted agents
+//               ranked by parent id (directly, or by binary search over the
+//               sorted tiles) and placed after the sorted agents
 //   k_accept    final-edge rule and reaction application
 //
 // The engine never depends on storage order: every decision is a function
@@ -532,7 +534,9 @@ __device__ __forceinline__ uint32_t scan_tile(Buffers& B, uint32_t tile, uint32_
 // monitor sums added, released partners counted.  For every simulation:
 // births placed this step = min(reserved, limit), their prefix over the
 // simulations (births are appended after the sorted agents in simulation
-// order), the id of the first child and the new next id; the threshold
+// order) and the tiles of segments longer than kBirthTile (the sorter
+// blocks derive the same layout), the id of the first child and the new
+// next id; the threshold
 // monitor's evaluation of the state the step started from; the step counter
 // (the step index tau in flight for the proposal search, then advanced
 // unless frozen or failed); the live counts' next-id entry.  Then the

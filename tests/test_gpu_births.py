@@ -115,3 +115,30 @@ def test_a_simulation_over_its_births_limit_stops_alone(A, oracle_mod):
     assert_same_dump(bt.dump(good), o.dump(), "after 30 steps")
     o.close()
     bt.close()
+
+
+def test_long_and_short_segments_in_one_batch_equal_the_oracle(A, oracle_mod):
+    """A long births segment (more than 2,048 births a step: ranked through
+    sorted tiles) between two short ones (ranked directly), so that blocks
+    of the ranking hold births of two simulations: digests every step and
+    the dumps at the end equal the oracle's."""
+    sims = [(W.births(300), 41), (W.births(2000), 42), (W.births(250), 43)]
+    cap_a, cap_c = A.batch_capacity([m for m, _ in sims], headroom=8.0)
+    bt = A.Batch(cap_a, cap_c, 3)
+    ids = [bt.add(m, s) for m, s in sims]
+    orcs = [oracle_mod.OracleSim(m, s) for m, s in sims]
+    prev = int(orcs[1].counts()[-1])
+    loads = []
+    for t in range(1, 13):
+        bt.step(1)
+        for k, (sid, o) in enumerate(zip(ids, orcs)):
+            o.step(1)
+            assert bt.digest(sid) == o.digest(), f"sim {k} step {t}"
+        c = int(orcs[1].counts()[-1])
+        loads.append(c - prev)
+        prev = c
+    assert min(loads[2:]) > 2048, loads                  # the middle segment takes the sorted path
+    for k, (sid, o) in enumerate(zip(ids, orcs)):
+        assert_same_dump(bt.dump(sid), o.dump(), f"sim {k} after 12 steps")
+        o.close()
+    bt.close()
