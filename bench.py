@@ -96,56 +96,102 @@ def molecules(counts, model):
 
 # ---------------------------------------------------------------------------
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons in the background."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling of SM clocks and throttle reasons in the background.
+
+    Every sample carries nvidia-smi's own timestamp, so the summary does not
+    depend on how the pipe is buffered.  ``__enter__`` waits (up to a second)
+    for the first sample so that the sampler is running when the caller's
+    timed region starts, and ``mark(t0, t1)`` (``time.perf_counter`` values)
+    names that region.  The summary is taken over the samples inside it; a
+    region shorter than the sampling interval falls back to the two samples
+    that bracket it, and ``window`` says which."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.region = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.lines.append(line)
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(self.index)],
+                                          "-lms", str(self.INTERVAL_MS), "-i", str(self.index)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t_end = time.perf_counter() + 1.0
+        while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+            time.sleep(0.005)
         return self
 
+    def mark(self, t0, t1):
+        # perf_counter -> wall-clock seconds, the clock nvidia-smi stamps with
+        off = time.time() - time.perf_counter()
+        self.region = (t0 + off, t1 + off)
+
     def __exit__(self, *a):
-        self.lines = []
         if self.proc:
+            time.sleep(3 * self.INTERVAL_MS / 1000.0)     # let one sample land after the region
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+                self.proc.wait()
+            self.reader.join(timeout=5)
+
+    @staticmethod
+    def parse(line):
+        """One CSV sample -> (epoch seconds, sm MHz, max MHz, watts, [active reasons]) or None."""
+        import datetime
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10:
+            return None
+        try:
+            sm, mx, pw = float(f[2]), float(f[3]), float(f[4])
+        except ValueError:
+            return None
+        try:
+            t = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            t = None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        return t, sm, mx, pw, [nm for nm, v in zip(names, f[6:10]) if v.lower() == "active"]
 
     def summary(self):
-        sm, mx, pw, reasons = [], [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
-            f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-                pw.append(float(f[3]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        rows = [r for r in map(self.parse, self.lines) if r]
+        window = "whole sampler run"
+        if rows and any(r[0] is None for r in rows):
+            window = "whole sampler run (timestamps unreadable)"
+        elif self.region and rows:
+            t0, t1 = self.region
+            slack = self.INTERVAL_MS / 1000.0
+            inside = [r for r in rows if t0 <= r[0] <= t1 + slack]
+            if inside:
+                rows, window = inside, "timed region"
+            else:
+                rows = [r for r in rows if r[0] < t0][-1:] + [r for r in rows if r[0] > t1][:1]
+                window = "the two samples bracketing the timed region (shorter than the interval)"
+        if not rows:
             return None
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm),
-                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+        sm = sorted(r[1] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[2] for r in rows), "samples": len(rows),
+                "interval_ms": self.INTERVAL_MS, "window": window,
+                "power_w_max": max(r[3] for r in rows),
+                "reasons": sorted({nm for r in rows for nm in r[4]})}
 
 
 def measured_peaks():
@@ -459,6 +505,7 @@ def main():
             ends[k].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        clk.mark(wall0, wall0 + wall)
     sim.sync()
     if dist:
         dist.barrier()
