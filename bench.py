@@ -484,8 +484,11 @@ def main():
             flush.zero_()
             flush_src.sum()
 
-    # warm-up (untimed)
+    # warm-up (untimed); one flush too, so that loading the flush's kernels
+    # falls outside the timed region
     sim.step(args.warmup)
+    if flush is not None:
+        flush_l2()
     sim.sync()
     n_before = molecules(sim.counts(), model)
 
