@@ -243,8 +243,8 @@ abm_status  abm_batch_sync(abm_batch* b);
 abm_status  abm_batch_sim_status(abm_batch* b, int32_t sim_id);
 /* Pipelined counts (the readout of Sec. 2, at every step if wanted, without
  * stalling the device): _begin queues the count pass for the state after the
- * steps issued so far and its copy into pinned host slot `slot` (0 ..
- * ABM_READ_SLOTS - 1) and returns at once; _finish waits for that slot and
+ * steps issued so far and a one-block kernel that writes the counts into
+ * pinned host slot `slot` (0 .. ABM_READ_SLOTS - 1), and returns at once; _finish waits for that slot and
  * writes the counts (layout as abm_batch_counts) to out[0..cap).  A caller
  * that steps, begins slot k % 2 and finishes slot (k - 1) % 2 keeps the
  * device busy while it reads.  ABM_EINVAL for a bad slot, _begin on a slot

@@ -311,6 +311,7 @@ struct abm_batch {
     uint64_t* h_counts = nullptr;        // ... and one simulation's counts (512 words)
     struct ReadSlot {                    // pipelined counts reads
         uint64_t* host = nullptr;        // pinned: 512 counts, then a copy of the control block
+        uint64_t* dev = nullptr;         // the same memory as the device addresses it
         cudaEvent_t done = nullptr;
         uint32_t n = 0;
         int32_t sim = -1;
@@ -603,6 +604,7 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     }
     for (auto& r : b->rs)
         if (cudaMallocHost((void**)&r.host, 8 * 512 + sizeof(Ctl)) != cudaSuccess ||
+            cudaHostGetDevicePointer((void**)&r.dev, r.host, 0) != cudaSuccess ||
             cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return destroy_and(ABM_ENOMEM);
@@ -1174,9 +1176,9 @@ abm_status abm_batch_counts_begin(abm_batch* b, int32_t sim, uint32_t slot) {
     auto& r = b->rs[slot];
     r.n = b->sims[sim].n_counts;
     r.sim = sim;
-    // stream order keeps a later reset of these counts behind this copy
-    CU(cudaMemcpyAsync(r.host, src + (size_t)sim * 512, 8 * (size_t)r.n, cudaMemcpyDeviceToHost, b->stream));
-    CU(cudaMemcpyAsync(r.host + 512, b->B.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    // one block writes the counts and the control words into the pinned slot;
+    // stream order keeps a later reset of these counts behind it
+    CU(launch_readout(src + (size_t)sim * 512, r.n, b->B.ctl, r.dev, b->stream));
     CU(cudaEventRecord(r.done, b->stream));
     r.pending = true;
     return ABM_OK;

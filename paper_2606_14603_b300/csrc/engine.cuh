@@ -349,6 +349,9 @@ cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32
 // Threshold monitor of one simulation at the current state (between steps):
 // adds up its value if that state is due and not yet evaluated, then evaluates.
 cudaError_t launch_monitor(const Buffers& B, const Launch& L, cudaStream_t s, int32_t sim);
+// Counts vector (n <= 512 words) and control words into a pinned host slot of
+// 512 + sizeof(Ctl) / 8 words (device-visible under unified addressing).
+cudaError_t launch_readout(const uint64_t* src, uint32_t n, const Ctl* ctl, uint64_t* dst, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                                 cudaStream_t s);
 

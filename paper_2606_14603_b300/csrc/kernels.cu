@@ -1419,6 +1419,25 @@ cudaError_t launch_dump(const Buffers& B, const Launch& L, cudaStream_t s, int32
     return cudaGetLastError();
 }
 
+// One simulation's counts vector (n words from src) and the control words,
+// written by one block straight into a pinned host slot: the host sees them
+// once an event recorded after this launch has completed.  One launch in
+// stream order behind the step, where two copy-engine transfers would each
+// wait for the step and hold the next one back.
+__global__ void __launch_bounds__(kThreads) k_readout(const uint64_t* __restrict__ src, uint32_t n,
+                                                      const Ctl* __restrict__ ctl, uint64_t* dst) {
+    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+    const uint32_t* c = reinterpret_cast<const uint32_t*>(ctl);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst + 512);
+    for (uint32_t k = threadIdx.x; k < sizeof(Ctl) / 4; k += blockDim.x) d[k] = c[k];
+    __threadfence_system();
+}
+
+cudaError_t launch_readout(const uint64_t* src, uint32_t n, const Ctl* ctl, uint64_t* dst, cudaStream_t s) {
+    k_readout<<<1, kThreads, 0, s>>>(src, n, ctl, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n,
                                 cudaStream_t s) {
     if (n == 0) return cudaSuccess;
