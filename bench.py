@@ -30,8 +30,8 @@ UNIT = "molecule-steps/s"
 # design; the step as a whole must read and rewrite the 20-byte agent record
 STEP_BYTES_PER_AGENT = 40
 E2E_STEPS = 500          # steps of the end-to-end loop (creation amortised over them)
-KERNEL_BYTES = {"k_move": (40, "agent"), "k_tile_prefix": (8 / 8192, "cell"), "k_scan": (12, "cell"),
-                "k_scatter": (53, "agent"), "k_propose": (24, "agent"), "k_accept": (4, "agent")}
+KERNEL_BYTES = {"k_move": (36, "agent"), "k_tile_prefix": (8 / 8192, "cell"), "k_scan": (12, "cell"),
+                "k_scatter": (45, "agent"), "k_propose": (20, "agent"), "k_accept": (4, "agent")}
 
 
 def parse():

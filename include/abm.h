@@ -109,6 +109,10 @@ typedef struct {
     double                 dt_s;          /* time step, > 0                */
     double                 unit_nm;       /* position quantum, > 0 (0.1)   */
 } abm_model;
+/* The root's edge (cube) or diameter (sphere), in units of unit_nm, must
+ * lie in [2, 2^21): positions are stored in 21 bits per axis (209.7 um at
+ * 0.1 nm).  Outside that range abm_create and abm_batch_add return
+ * ABM_EINVAL. */
 
 /* Options of a single simulation.  Zero-initialise and set what you need. */
 typedef struct {

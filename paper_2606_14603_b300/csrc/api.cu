@@ -123,7 +123,7 @@ abm_status compile_model(const abm_model* m, Compiled* c, std::string* err) {
     } else {
         return bad("unknown root shape");
     }
-    if (ext < 2 || ext >= (1ll << 30)) return bad("root extent must be in [2, 2^30) units");
+    if (ext < 2 || ext >= kPosLimit) return bad("root extent must be in [2, 2^21) position units");
     g.ext = (int32_t)ext;
     g.n_comp = (int32_t)n_comp;
     for (uint32_t k = 1; k < n_comp; k++) {
@@ -260,10 +260,10 @@ Layout layout_for(uint64_t C, uint64_t K, uint32_t S, uint32_t Bc) {
     const uint64_t Kpad = (K + kTile - 1) / kTile * kTile;
     const uint64_t tiles = Kpad / kTile + 1;
     const size_t sizes[] = {
-        16 * C, 16 * C,                        // pm[2]
-        4 * C, 4 * C, 4 * C, 4 * C,            // aid[2], apar[2]
+        16 * C, 16 * C,                        // pm[2] (packed records with ids)
+        4 * C, 4 * C,                          // apar[2]
         4 * C, 8 * C, 8 * C, (size_t)C,        // rk, acc, props, pflag
-        16 * E, 4 * E, 4 * E,                  // extras
+        16 * E, 4 * E,                         // extras: records, ranks
         8 * (size_t)Bc * S, 4 * ((size_t)S + 1),  // births: one segment per simulation slot, prefixes
         4 * (size_t)Bc * S, 4 * ((size_t)S + 1),  // sorted tiles of long births segments, their prefixes
         4 * Kpad, 4 * (Kpad + 8),              // cnt, start
@@ -615,8 +615,6 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     Buffers& B = b->B;
     B.pm[0] = (int4*)at();
     B.pm[1] = (int4*)at();
-    B.aid[0] = (uint32_t*)at();
-    B.aid[1] = (uint32_t*)at();
     B.apar[0] = (uint32_t*)at();
     B.apar[1] = (uint32_t*)at();
     B.rk = (uint32_t*)at();
@@ -624,7 +622,6 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     B.props = (uint2*)at();
     B.pflag = (uint8_t*)at();
     B.xpm = (int4*)at();
-    B.xid = (uint32_t*)at();
     B.xrk = (uint32_t*)at();
     B.bseg = (uint2*)at();
     B.bofs = (uint32_t*)at();
@@ -677,6 +674,16 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     b->L.threads_move = tm;
     b->L.blocks_move = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((b->cap_agents + tm - 1) / tm, (uint64_t)sms * per_sm));
+    // the scatter needs fewer registers than the move pass: on large batches
+    // all of its blocks that fit at once (measured: 16M agents 530 -> 512 us
+    // per step); up to 2M agents the move pass's grid (the larger grid cost
+    // 1M agents about 1 us)
+    const bool large = b->cap_agents > (2ull << 20);
+    const uint64_t per_sm_scatter =
+        o->blocks_per_sm ? o->blocks_per_sm
+                         : (large ? (uint64_t)std::max(scatter_blocks_per_sm(tm), (int)per_sm) : per_sm);
+    b->L.blocks_scatter = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((b->cap_agents + tm - 1) / tm, (uint64_t)sms * per_sm_scatter));
     uint64_t chunk = 1024;
     while (chunk < 4096 && chunk * (uint64_t)sms * 8 < b->cap_agents) chunk *= 2;
     if (o->propose_chunk) chunk = o->propose_chunk;
@@ -909,13 +916,16 @@ static abm_status add_sim(abm_batch* b, const abm_model* model, uint64_t seed, u
     CU(cudaMemcpyAsync(b->staging, c->species_end, 4 * kMaxSpecies, cudaMemcpyHostToDevice, b->stream));
     const uint32_t nsu = b->n_sims_used;
     CU(cudaMemcpyAsync(&b->B.ctl->n_sims, &nsu, 4, cudaMemcpyHostToDevice, b->stream));
+    std::vector<int4> packed;  // (uploaded asynchronously: alive until the synchronisation below)
     if (restore) {
-        for (auto& p : rs.pm) p.w |= (int)((uint32_t)slot << M_SIM_SHIFT);
         const size_t k = rs.pm.size();
+        packed.resize(k);
+        for (size_t i = 0; i < k; i++) {
+            rs.pm[i].w |= (int)((uint32_t)slot << M_SIM_SHIFT);
+            packed[i] = repack(rs.pm[i], rs.id[i]);
+        }
         if (k) {
-            CU(cudaMemcpyAsync(b->B.pm[h.cur] + h.n_buf[h.cur], rs.pm.data(), 16 * k, cudaMemcpyHostToDevice,
-                               b->stream));
-            CU(cudaMemcpyAsync(b->B.aid[h.cur] + h.n_buf[h.cur], rs.id.data(), 4 * k, cudaMemcpyHostToDevice,
+            CU(cudaMemcpyAsync(b->B.pm[h.cur] + h.n_buf[h.cur], packed.data(), 16 * k, cudaMemcpyHostToDevice,
                                b->stream));
             CU(cudaMemcpyAsync(b->B.apar[h.cur] + h.n_buf[h.cur], rs.par.data(), 4 * k, cudaMemcpyHostToDevice,
                                b->stream));

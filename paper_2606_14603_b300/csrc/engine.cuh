@@ -1,15 +1,16 @@
 // engine.cuh — device-side data layout and helpers of the step engine.
 //
 // Layout in HBM (one arena per batch, 256-byte aligned sub-buffers):
-//   pm[2][C]     int4 {x, y, z, meta}   agent record, double-buffered
-//   aid[2][C]    u32 agent id           (ids are per simulation)
+//   pm[2][C]     int4 agent record, double-buffered: the position packed as
+//                x | y << 21 | z << 42 in the first two words (positions in
+//                [0, 2^21) units), the meta word, the agent id (per simulation)
 //   apar[2][C]   u32 partner id         (valid for carriers only)
 //   rk[C]        u32 rank within the new cell, from the move pass (the
 //                scatter finds the cell again from the moved record)
 //   acc[C]       u64 proposal slot, min of (dist^2 << 32 | proposer id)
 //   props[C]     (proposer, target) sorted indices of this step's proposals
 //   pflag[C]     1 if the sorted agent is a free proposer (written by the scatter)
-//   xpm/xid/xrk  released partners appended by the move pass (C/2 + 1)
+//   xpm/xrk      released partners appended by the move pass (C/2 + 1): record, rank
 //   bseg[S][Q]   births of the step, one segment of Q per simulation slot:
 //                (parent's slot in the moved buffer, parent id)
 //   bofs[S+1]    births placed before each simulation this step (prefix)
@@ -171,15 +172,13 @@ struct Ctl {
 };
 
 struct Buffers {
-    int4* pm[2];
-    uint32_t* aid[2];
+    int4* pm[2];             // packed records (pack_rec)
     uint32_t* apar[2];
     uint32_t* rk;            // per agent: rank within its new cell (kNone: not placed)
     uint64_t* acc;
     uint2* props;
     uint8_t* pflag;
     int4* xpm;
-    uint32_t* xid;
     uint32_t* xrk;
     uint2* bseg;             // [max sims][bquota] births: (parent slot, parent id)
     uint32_t* bofs;          // [max sims + 1] births before each simulation this step
@@ -209,6 +208,23 @@ struct Buffers {
     uint32_t live_stride;    // entries of one live-counts buffer (max sims x 512)
     uint32_t max_sims;       // simulation slots
 };
+
+// Packed agent record: the position x | y << 21 | z << 42 in words 0-1,
+// the meta word, the id.  Positions lie in [0, kPosLimit).
+constexpr int32_t kPosLimit = 1 << 21;
+__host__ __device__ __forceinline__ int4 pack_rec(int32_t x, int32_t y, int32_t z, uint32_t meta, uint32_t id) {
+    return make_int4((int)((uint32_t)x | (uint32_t)y << 21), (int)((uint32_t)y >> 11 | (uint32_t)z << 10),
+                     (int)meta, (int)id);
+}
+// The unpacked view {x, y, z, meta} of a packed record (its id is r.w).
+__host__ __device__ __forceinline__ int4 unpack_rec(int4 r) {
+    const uint32_t a = (uint32_t)r.x, b = (uint32_t)r.y;
+    return make_int4((int)(a & 0x1FFFFFu), (int)(a >> 21 | (b & 0x3FFu) << 11), (int)(b >> 10), r.z);
+}
+// A record from its unpacked view p ({x, y, z, meta}) and id.
+__host__ __device__ __forceinline__ int4 repack(const int4& p, uint32_t id) {
+    return pack_rec(p.x, p.y, p.z, (uint32_t)p.w, id);
+}
 
 // The live-counts buffer a step with this epoch fills.
 __device__ __forceinline__ uint64_t* live_buffer(const Buffers& B, uint32_t epoch) {
@@ -316,7 +332,8 @@ __device__ __forceinline__ bool mon_due(const MonDev& M, uint32_t t) {
 // Host-side launch wrappers (kernels.cu).
 struct Launch {
     int blocks_agents;       // grid of the between-step per-agent kernels (grid-stride, 256 threads)
-    int blocks_move;         // grid of k_move and k_scatter: the blocks of threads_move that fit at once
+    int blocks_move;         // grid of k_move: the blocks of threads_move that fit at once
+    int blocks_scatter;      // grid of k_scatter (same block size): the blocks that fit at once
     int threads_move;        // block size of k_move and k_scatter: 128, 256 or 512
     int threads;             // 256
     int blocks_scan;
@@ -328,6 +345,7 @@ struct Launch {
 // CTAs of k_move with `threads` threads that fit on one SM at once (its
 // registers decide); valid block sizes are 128, 256 and 512.
 int move_blocks_per_sm(int threads);
+int scatter_blocks_per_sm(int threads);
 bool valid_move_threads(int threads);
 size_t propose_smem(const Buffers& B);
 

@@ -194,8 +194,7 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, 
                     const uint32_t key = cell_of(S, q.x, q.y, q.z);
                     const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
                     atomicAdd(&B.tcnt[key / kScanTile * kTileStride], 1u);
-                    B.xpm[k] = q;
-                    B.xid[k] = par;
+                    B.xpm[k] = repack(q, par);
                     B.xrk[k] = rank;  // the scatter finds the cell again from q
                     if (ctl->live_counts)  // (rare: read here, not kept in registers)
                         atomicAdd((unsigned long long*)&live_buffer(B, ctl->epoch)[S.counts_off +
@@ -292,7 +291,7 @@ __device__ __forceinline__ void move_phase4(Buffers& B, Ctl* ctl, uint32_t cur, 
         return;
     }
     B.rk[i] = rank;  // the scatter finds the cell again from the moved record
-    B.pm[cur][i] = a.p;
+    B.pm[cur][i] = repack(a.p, a.id);
     if (a.flags & 2u) reserve_birth(B, ctl, parity, sim_of((uint32_t)a.p.w), i, a.id);
 }
 
@@ -308,7 +307,6 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
         ctl->move_parity = epoch & 1u;  // stable during k_scan, whose bookkeeping advances epoch
     }
     const int4* __restrict__ pm = B.pm[cur];
-    const uint32_t* __restrict__ aid = B.aid[cur];
     // proposal slots touched last step become empty again (the list is short)
     const uint32_t np = ctl->n_props[parity ^ 1u];
     const uint32_t stride = nb * blockDim.x;
@@ -317,7 +315,7 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
     // loop of its own: it keeps the main loop's register count)
     if (ctl->n_monitors)
         for (uint32_t i = bid * blockDim.x + threadIdx.x; i < n; i += stride)
-            monitor_record(B, (uint32_t)pm[i].w, kNone);
+            monitor_record(B, (uint32_t)pm[i].z, kNone);
     // Each warp takes a contiguous range of agents, 32 consecutive ones per
     // iteration (coalesced).  The next 32 records are loaded while these run
     // their chain of dependent table lookups and the histogram atomic.  The
@@ -340,27 +338,20 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
         for (uint32_t k = threadIdx.x; k < 512; k += blockDim.x) s_live[k] = 0;
         if (threadIdx.x == 0) {
             const uint32_t first = min(n, bid * (blockDim.x >> 5) * len);
-            s_live_sim = first < n ? sim_of((uint32_t)pm[first].w) : kNone;
+            s_live_sim = first < n ? sim_of((uint32_t)pm[first].z) : kNone;
         }
         __syncthreads();
     }
-    int4 nx_p = make_int4(0, 0, 0, 0);
-    uint32_t nx_id = 0;
-    if (wbeg + lane < wend) {
-        nx_p = pm[wbeg + lane];
-        nx_id = aid[wbeg + lane];
-    }
+    int4 nx_p = make_int4(0, 0, 0, 0);  // the next packed record
+    if (wbeg + lane < wend) nx_p = pm[wbeg + lane];
     uint32_t run_tile = kNone, run_n = 0;  // the same in every lane
     for (uint32_t base = wbeg; base < wend; base += 32) {  // uniform over the warp
         const uint32_t i = base + lane;
         MoveState a;
         a.flags = 0;
-        a.p = nx_p;
-        a.id = nx_id;
-        if (i + 32 < wend) {
-            nx_p = pm[i + 32];
-            nx_id = aid[i + 32];
-        }
+        a.p = unpack_rec(nx_p);
+        a.id = (uint32_t)nx_p.w;
+        if (i + 32 < wend) nx_p = pm[i + 32];
         if (i < wend) {
             move_phase1(B, ctl, cur, parity, i, a);
             move_phase2(a);
@@ -725,8 +716,8 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
     const uint32_t stride = nb * blockDim.x;
     for (uint32_t j0 = bid * blockDim.x + threadIdx.x; j0 < total; j0 += kScatterILP * stride) {
         uint32_t rk[kScatterILP];
-        int4 p[kScatterILP];
-        uint32_t id[kScatterILP], par[kScatterILP];
+        int4 p[kScatterILP];  // packed records
+        uint32_t par[kScatterILP];
 #pragma unroll
         for (int u = 0; u < kScatterILP; u++) {
             const uint32_t j = j0 + u * stride;
@@ -735,13 +726,11 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
             if (j < n_in) {
                 rk[u] = B.rk[j];
                 p[u] = B.pm[cur][j];
-                id[u] = B.aid[cur][j];
                 par[u] = B.apar[cur][j];
             } else if (j < total) {
                 const uint32_t k = j - n_in;
                 rk[u] = B.xrk[k];
                 p[u] = B.xpm[k];
-                id[u] = B.xid[k];
             }
         }
         // the cell comes from the moved record, as the move pass computed it
@@ -750,8 +739,9 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
         for (int u = 0; u < kScatterILP; u++) {
             dest[u] = kNone;
             if (rk[u] == kNone) continue;
-            const SimDev& S = B.sims[sim_of((uint32_t)p[u].w)];
-            dest[u] = B.start[cell_of(S, p[u].x, p[u].y, p[u].z)] + rk[u];
+            const SimDev& S = B.sims[sim_of((uint32_t)p[u].z)];
+            const int4 q = unpack_rec(p[u]);
+            dest[u] = B.start[cell_of(S, q.x, q.y, q.z)] + rk[u];
         }
 #pragma unroll
         for (int u = 0; u < kScatterILP; u++) {
@@ -760,9 +750,8 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
                 raise_error(ctl, ERR_CAPACITY_AGENTS, dest[u]);
                 continue;
             }
-            const uint32_t meta = (uint32_t)p[u].w;
+            const uint32_t meta = (uint32_t)p[u].z;
             B.pm[nxt][dest[u]] = p[u];
-            B.aid[nxt][dest[u]] = id[u];
             B.pflag[dest[u]] = (meta & (M_PROP | M_BOUND)) == M_PROP;
             if (meta & M_BOUND) B.apar[nxt][dest[u]] = par[u];
         }
@@ -797,13 +786,13 @@ struct Best {
 };
 
 __device__ __forceinline__ void consider(const SimDev& S, const ModelDev& Mo, const int4& p, uint32_t meta,
-                                         uint32_t sp, uint64_t mask, int rmax, uint32_t& ida, uint32_t gi,
-                                         const int4& q, uint32_t gj, const uint32_t* __restrict__ aid,
-                                         uint32_t t, Best& best) {
+                                         uint32_t sp, uint64_t mask, int rmax, uint32_t ida, const int4& qr,
+                                         uint32_t gj, uint32_t t, Best& best) {
     // cheap rejections first: almost every candidate is beyond every radius
+    const int4 q = unpack_rec(qr);
     const int dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
     if (abs(dx) > rmax || abs(dy) > rmax || abs(dz) > rmax) return;
-    const uint32_t mq = (uint32_t)q.w;
+    const uint32_t mq = (uint32_t)qr.z;
     if (mq & M_BOUND) return;
     if ((mq ^ meta) & M_COMP) return;
     const uint32_t spb = mq & M_SP;
@@ -812,10 +801,9 @@ __device__ __forceinline__ void consider(const SimDev& S, const ModelDev& Mo, co
     if (abs(dx) > R.R || abs(dy) > R.R || abs(dz) > R.R) return;
     const uint32_t d2 = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
     if (d2 > R.R2) return;
-    const uint32_t idb = aid[gj];
+    const uint32_t idb = (uint32_t)qr.w;
     const uint64_t key = (uint64_t)d2 << 32 | idb;
     if (key >= best.key) return;  // cannot win: the draw is not needed
-    if (ida == kNone) ida = aid[gi];
     const uint32_t lo = min(ida, idb), hi = max(ida, idb);
     const uint4 u = philox(make_uint4(lo, hi, t, 1u), S.key0, S.key1);
     if ((uint64_t)u.x >= R.thr_bind) return;
@@ -843,7 +831,6 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
                                               uint32_t* s_list, uint32_t* s_n) {
     const uint32_t cur = B.ctl->cur;  // the sorted buffer (flipped by this step's bookkeeping)
     const int4* __restrict__ pm = B.pm[cur];
-    const uint32_t* __restrict__ aid = B.aid[cur];
     const uint32_t* __restrict__ start = B.start;
     const uint32_t chunk = B.propose_chunk;
     // each thread takes chunk / 256 consecutive flags (4, 8 or 16 bytes, read
@@ -875,7 +862,8 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
     int4 p_n = threadIdx.x < np ? pm[gi_n] : make_int4(0, 0, 0, 0);
     for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
         const uint32_t gi = gi_n;
-        const int4 p = p_n;
+        const int4 p = unpack_rec(p_n);
+        const uint32_t ida = (uint32_t)p_n.w;
         if (k + blockDim.x < np) {
             gi_n = s_list[k + blockDim.x];
             p_n = pm[gi_n];
@@ -892,12 +880,11 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
         const int ylo = max((p.y - rmax) >> sh, 0), yhi = min((p.y + rmax) >> sh, g - 1);
         const int zlo = max((p.z - rmax) >> sh, 0), zhi = min((p.z + rmax) >> sh, g - 1);
         Best best;
-        uint32_t ida = kNone;
         // x-consecutive cells of one (z, y) row form one contiguous range of
         // the sorted array, walked one candidate record at a time
         auto walk = [&](uint32_t a, uint32_t b) {
             for (uint32_t j = a; j < b; j++)
-                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, pm[j], j, aid, S.tau, best);
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, pm[j], j, S.tau, best);
         };
         if (zhi - zlo <= 1 && yhi - ylo <= 1) {
             // the usual box (2 * rmax below the cell edge): at most 2 x 2 rows,
@@ -929,7 +916,7 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
                     jn = cand(t + 1);
                     qn = pm[jn];
                 }
-                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, gi, q, j, aid, S.tau, best);
+                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, q, j, S.tau, best);
             }
         } else {
             // a box wider than half a cell can meet 3 cells per axis (a cell is
@@ -1017,13 +1004,13 @@ __device__ __noinline__ void place_births(Buffers& B, uint32_t cur, uint32_t nbt
         }
         const SimDev& S = B.sims[s];
         const ModelDev& Mo = B.models[S.model];
-        int4 q = B.pm[src][seg[k].x];
-        const uint32_t meta = (uint32_t)q.w;
-        q.w = (int)with_species(meta & ~(M_RXN | M_BOUND | M_ROLE_A), (uint32_t)Mo.sp[meta & M_SP].emit, Mo);
+        int4 q = B.pm[src][seg[k].x];  // the parent's packed record: its place
+        const uint32_t meta = (uint32_t)q.z;
+        q.z = (int)with_species(meta & ~(M_RXN | M_BOUND | M_ROLE_A), (uint32_t)Mo.sp[meta & M_SP].emit, Mo);
+        q.w = (int)(S.nid0 + rank);
         const uint32_t dst = ns + s_bofs[s] + rank;
         B.pm[cur][dst] = q;
-        B.aid[cur][dst] = S.nid0 + rank;
-        if (live) atomicAdd((unsigned long long*)&live[S.counts_off + count_slot((uint32_t)q.w, Mo)], 1ull);
+        if (live) atomicAdd((unsigned long long*)&live[S.counts_off + count_slot((uint32_t)q.z, Mo)], 1ull);
     }
 }
 
@@ -1058,18 +1045,18 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
     const uint32_t np = ctl->n_props[parity];
     uint64_t* live = ctl->live_counts ? live_buffer(B, epoch - 1u) : nullptr;
     int4* __restrict__ pm = B.pm[cur];
-    uint32_t* __restrict__ aid = B.aid[cur];
     uint32_t* __restrict__ apar = B.apar[cur];
     for (uint32_t k = bid * blockDim.x + threadIdx.x; k < np; k += nb * blockDim.x) {
         const uint2 e = B.props[k];
         const uint32_t i = e.x, j = e.y;
-        // the two meta words are loaded with the slots (one round trip less)
-        uint32_t* wa = reinterpret_cast<uint32_t*>(&pm[i]) + 3;
-        uint32_t* wb = reinterpret_cast<uint32_t*>(&pm[j]) + 3;
+        // the (meta, id) words of both records are loaded with the slots (one round trip less)
+        uint2* wa = reinterpret_cast<uint2*>(&pm[i]) + 1;
+        uint2* wb = reinterpret_cast<uint2*>(&pm[j]) + 1;
         const uint64_t kb = B.acc[j];
-        const uint32_t ida = aid[i];
         const uint64_t ka = B.acc[i];
-        uint32_t ma = *wa, mb = *wb;
+        const uint2 ra = *wa, rb = *wb;
+        const uint32_t ida = ra.y;
+        uint32_t ma = ra.x, mb = rb.x;
         if ((uint32_t)kb != ida || ka != kEmpty) continue;
         const uint32_t ma0 = ma, mb0 = mb;
         const SimDev& S = B.sims[sim_of(ma)];
@@ -1081,15 +1068,15 @@ __device__ __forceinline__ void accept_pass(Buffers& B, uint32_t bid, uint32_t n
             mb = R.prod_b >= 0 ? with_species(mb, (uint32_t)R.prod_b, Mo) : mb | M_DEAD;
         } else if (R.carrier_a) {  // BIND, a carries b
             ma |= M_BOUND | M_ROLE_A | (r << M_RXN_SHIFT);
-            apar[i] = aid[j];
+            apar[i] = rb.y;
             mb |= M_ABSORBED;
         } else {  // BIND, b carries a
             mb |= M_BOUND | (r << M_RXN_SHIFT);
             apar[j] = ida;
             ma |= M_ABSORBED;
         }
-        *wa = ma;
-        *wb = mb;
+        reinterpret_cast<uint32_t*>(wa)[0] = ma;
+        reinterpret_cast<uint32_t*>(wb)[0] = mb;
         if (live) {  // the move pass counted both as they were
             unsigned long long* L = (unsigned long long*)live + S.counts_off;
             atomicAdd(L + count_slot(ma0, Mo), ~0ull);
@@ -1133,8 +1120,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Buffers B, uint32_t sim, uint
         }
         if (!placed) raise_error(ctl, ERR_PLACEMENT, k);
         const uint32_t meta = with_species((sim << M_SIM_SHIFT) | ((uint32_t)want << M_COMP_SHIFT), sp, Mo);
-        B.pm[cur][base + k] = make_int4(x, y, z, (int)meta);
-        B.aid[cur][base + k] = k;
+        B.pm[cur][base + k] = pack_rec(x, y, z, meta, k);
     }
 }
 
@@ -1145,9 +1131,10 @@ __global__ void __launch_bounds__(kThreads) k_init(Buffers B, uint32_t sim, uint
 // Each block owns one contiguous range of the cell-sorted array, so almost
 // all of its agents belong to one simulation: those are counted in a
 // shared-memory histogram and flushed with one atomic per bin.
-__device__ __forceinline__ void observe_one(Buffers& B, uint32_t cur, uint32_t i, const int4& p, int32_t only_sim,
+__device__ __forceinline__ void observe_one(Buffers& B, uint32_t cur, uint32_t i, const int4& pr, int32_t only_sim,
                                             int want_digest, uint32_t sim0, uint32_t* sh) {
-    const uint32_t meta = (uint32_t)p.w;
+    const uint32_t meta = (uint32_t)pr.z;
+    const int4 p = unpack_rec(pr);
     if (meta & (M_DEAD | M_ABSORBED)) return;
     const uint32_t s = sim_of(meta);
     if (only_sim >= 0 && s != (uint32_t)only_sim) return;
@@ -1162,7 +1149,7 @@ __device__ __forceinline__ void observe_one(Buffers& B, uint32_t cur, uint32_t i
         slot = Mo.n_sp * Mo.n_comp + r;
         if (want_digest) {
             const ReactionDev& R = Mo.rx[r];
-            const uint32_t id = B.aid[cur][i];
+            const uint32_t id = (uint32_t)pr.w;
             const uint32_t par = B.apar[cur][i];
             const bool ra = meta & M_ROLE_A;
             h = record_hash(id, sp, comp, 1u | (ra ? 4u : 0u), r, p.x, p.y, p.z, par);
@@ -1170,7 +1157,7 @@ __device__ __forceinline__ void observe_one(Buffers& B, uint32_t cur, uint32_t i
         }
     } else {
         slot = sp * Mo.n_comp + comp;
-        if (want_digest) h = record_hash(B.aid[cur][i], sp, comp, 0u, 0xFFu, p.x, p.y, p.z, kNone);
+        if (want_digest) h = record_hash((uint32_t)pr.w, sp, comp, 0u, 0xFFu, p.x, p.y, p.z, kNone);
     }
     if (s == sim0) atomicAdd(&sh[slot], 1u);
     else atomicAdd((unsigned long long*)&B.counts[S.counts_off + slot], 1ull);
@@ -1197,7 +1184,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
     if (threadIdx.x == 0) {
         uint32_t s0 = kNone;
         if (only_sim >= 0) s0 = (uint32_t)only_sim;
-        else if (begin < end) s0 = sim_of((uint32_t)B.pm[cur][begin].w);
+        else if (begin < end) s0 = sim_of((uint32_t)B.pm[cur][begin].z);
         s_sim = s0;
     }
     __syncthreads();
@@ -1208,7 +1195,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(Buffers B, int32_t only_si
 #pragma unroll
         for (int u = 0; u < kObserveILP; u++) {
             const uint32_t i = i0 + u * blockDim.x;
-            p[u] = i < end ? B.pm[cur][i] : make_int4(0, 0, 0, (int)M_DEAD);
+            p[u] = i < end ? B.pm[cur][i] : make_int4(0, 0, (int)M_DEAD, 0);
         }
 #pragma unroll
         for (int u = 0; u < kObserveILP; u++) observe_one(B, cur, i0 + u * blockDim.x, p[u], only_sim, want_digest, sim0, sh);
@@ -1243,7 +1230,7 @@ __global__ void __launch_bounds__(kThreads) k_monitor_pass(Buffers B, uint32_t s
     const SimDev& S = B.sims[sim];
     if (!S.active || !mon_due(B.mons[sim], S.step)) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        monitor_record(B, (uint32_t)B.pm[cur][i].w, sim);
+        monitor_record(B, (uint32_t)B.pm[cur][i].z, sim);
 }
 
 __global__ void k_monitor_eval(Buffers B, uint32_t sim) { monitor_eval(B, sim); }
@@ -1257,12 +1244,11 @@ __global__ void __launch_bounds__(kThreads) k_compact(Buffers B) {
     const uint32_t n = ctl->n_buf[cur];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int4 p = B.pm[cur][i];
-        const uint32_t meta = (uint32_t)p.w;
+        const uint32_t meta = (uint32_t)p.z;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
         if (!B.sims[sim_of(meta)].active) continue;
         const uint32_t k = reserve(&ctl->n_compact);
         B.pm[nxt][k] = p;
-        B.aid[nxt][k] = B.aid[cur][i];
         if (meta & M_BOUND) B.apar[nxt][k] = B.apar[cur][i];
     }
 }
@@ -1276,12 +1262,13 @@ __global__ void __launch_bounds__(kThreads) k_dump(Buffers B, int32_t sim, uint4
     const SimDev& S = B.sims[sim];
     const ModelDev& Mo = B.models[S.model];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int4 p = B.pm[cur][i];
-        const uint32_t meta = (uint32_t)p.w;
+        const int4 pr = B.pm[cur][i];
+        const uint32_t meta = (uint32_t)pr.z;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
         if (sim_of(meta) != (uint32_t)sim) continue;
+        const int4 p = unpack_rec(pr);
         const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
-        const uint32_t id = B.aid[cur][i];
+        const uint32_t id = (uint32_t)pr.w;
         const bool bound = meta & M_BOUND;
         const uint32_t k = atomicAdd(&ctl->dump_n, bound ? 2u : 1u);
         if (k + (bound ? 2u : 1u) > cap) continue;  // host sees dump_n > cap
@@ -1357,12 +1344,20 @@ int move_blocks_per_sm(int threads) {
     return n;
 }
 
+int scatter_blocks_per_sm(int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, move_kernels(threads).scatter, threads, 0) != cudaSuccess ||
+        n < 1)
+        n = 1024 / threads;
+    return n;
+}
+
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool live) {
     const MoveKernels mk = move_kernels(L.threads_move);
     cudaError_t e = launch_pdl(live ? mk.move_live : mk.move, L.blocks_move, s, B, 0, L.threads_move);
     if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1 + kSortBlocks, s, B);
-    if (e == cudaSuccess) e = launch_pdl(mk.scatter, L.blocks_move, s, B, 0, L.threads_move);
+    if (e == cudaSuccess) e = launch_pdl(mk.scatter, L.blocks_scatter, s, B, 0, L.threads_move);
     if (e == cudaSuccess) e = launch_pdl(k_propose, L.blocks_propose, s, B, propose_smem(B));
     if (e == cudaSuccess) e = launch_pdl(k_accept, L.blocks_accept, s, B);
     return e;
@@ -1377,7 +1372,7 @@ cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s,
     cudaEventRecord(ev[2], s);
     k_scan<<<L.blocks_scan + 1 + kSortBlocks, kThreads, 0, s>>>(B);
     cudaEventRecord(ev[3], s);
-    mk.scatter<<<L.blocks_move, L.threads_move, 0, s>>>(B);
+    mk.scatter<<<L.blocks_scatter, L.threads_move, 0, s>>>(B);
     cudaEventRecord(ev[4], s);
     k_propose<<<L.blocks_propose, kThreads, propose_smem(B), s>>>(B);
     cudaEventRecord(ev[5], s);

@@ -54,12 +54,13 @@ __global__ void __launch_bounds__(256) k_dump_static(Buffers B, int32_t sim, Dum
     const SimDev& S = B.sims[sim];
     const ModelDev& Mo = B.models[S.model];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int4 p = B.pm[cur][i];
-        const uint32_t meta = (uint32_t)p.w;
+        const int4 pr = B.pm[cur][i];
+        const uint32_t meta = (uint32_t)pr.z;
         if (meta & (M_DEAD | M_ABSORBED)) continue;
         if (sim_of(meta) != (uint32_t)sim) continue;
+        const int4 p = unpack_rec(pr);
         const uint32_t sp = meta & M_SP, comp = (meta & M_COMP) >> M_COMP_SHIFT;
-        const uint32_t id = B.aid[cur][i];
+        const uint32_t id = (uint32_t)pr.w;
         const bool bound = meta & M_BOUND;
         const uint32_t k = atomicAdd(&sc->count, bound ? 2u : 1u);
         if (k + (bound ? 2u : 1u) > kNoAllocRecords) continue;  // counted, not written
