@@ -726,7 +726,6 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
             if (j < n_in) {
                 rk[u] = B.rk[j];
                 p[u] = B.pm[cur][j];
-                par[u] = B.apar[cur][j];
             } else if (j < total) {
                 const uint32_t k = j - n_in;
                 rk[u] = B.xrk[k];
@@ -742,6 +741,8 @@ __device__ __forceinline__ void scatter_pass(Buffers& B, uint32_t bid, uint32_t 
             const SimDev& S = B.sims[sim_of((uint32_t)p[u].z)];
             const int4 q = unpack_rec(p[u]);
             dest[u] = B.start[cell_of(S, q.x, q.y, q.z)] + rk[u];
+            // the partner id only for carriers (few), requested beside the start[] gather
+            if (((uint32_t)p[u].z & M_BOUND) && j0 + u * stride < n_in) par[u] = B.apar[cur][j0 + u * stride];
         }
 #pragma unroll
         for (int u = 0; u < kScatterILP; u++) {
