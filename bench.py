@@ -554,7 +554,8 @@ def main():
             "bytes_per_unit": bpu, "units_per_launch": units, "unit_of_work": unit_name,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.4 TB/s",
             "kernel_ms": dom_ms,
-            "kernel_ms_is": "CUDA events around the kernel, step launched without the graph (frac uses this)",
+            "kernel_ms_is": ("CUDA events around the kernel, the step's kernels serialised (no overlap between "
+                             "kernels), events and launches replayed as one graph (frac uses this)"),
             "kernel_ms_graph_est": dom_ms_graph,
             "frac_graph_est": bpu * units / (dom_ms_graph / 1e3) / 1e9 / hbm,
             "traffic_source": (f"ncu {traffic[3]}" if traffic and len(traffic) > 3 else None)}

@@ -356,8 +356,11 @@ abm_status  abm_monitor_read(abm_sim* sim, abm_monitor_state* out, int64_t* trac
 abm_status  abm_dump_noalloc(abm_sim* sim, abm_record* out, size_t cap, size_t* n_out);
 
 /* ---------------- profiling ---------------- */
-/* Runs n steps without the CUDA graph, with a CUDA event on the stream
- * before and after each of the step's kernels, and writes the summed time of
+/* Runs n steps with a CUDA event on the stream before and after each of the
+ * step's kernels (the kernels launched one after another, without the
+ * step's overlap between consecutive kernels; the launches and events are
+ * replayed as one CUDA graph, captured on first use, so that host launch
+ * latency falls outside the timed intervals), and writes the summed time of
  * each kernel in milliseconds to kernel_ms[0..5] (n_kernels >= 6; names from
  * abm_kernel_name; slot 1, k_tile_prefix, runs only on grids of more than
  * 8192 tiles of 8192 cells and reads 0 otherwise).  Synchronous.  The state

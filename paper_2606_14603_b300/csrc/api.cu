@@ -323,6 +323,11 @@ struct abm_batch {
     bool live_valid = false;             // live counts hold the current state (a step ran with them on)
     cudaGraphExec_t g1 = nullptr, g8 = nullptr;
     cudaGraphExec_t g1_live = nullptr, g8_live = nullptr;  // the same with live counts, captured on first use
+    // abm_profile_step: one step's kernels with an event before and after each,
+    // as a graph (so that no host launch gap falls between an event and its
+    // kernel), captured on first use, without and with live counts
+    cudaGraphExec_t gprof[2] = {nullptr, nullptr};
+    cudaEvent_t prof_ev[kStepKernels + 1] = {};
     uint32_t sim_errs_seen = 0;          // per-simulation errors already read from the device
     struct HostSim {
         int state = 0;  // 0 free, 1 active, 2 draining (removed, not yet stepped)
@@ -1101,20 +1106,36 @@ abm_status abm_batch_profile_step(abm_batch* b, uint32_t n, float* kernel_ms, ui
     if (n > 0)
         for (auto& h : b->sims)
             if (h.state == 2) h.state = 0;
-    cudaEvent_t ev[kStepKernels + 1];
-    for (int k = 0; k <= kStepKernels; k++) CU(cudaEventCreate(&ev[k]));
+    const int mode = b->live_on != 0;
+    if (!b->prof_ev[0])
+        for (auto& e : b->prof_ev) CU(cudaEventCreate(&e));
+    if (!b->gprof[mode]) {
+        cudaStream_t cs;
+        CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t el = launch_step_timed(b->B, b->L, cs, b->prof_ev, mode != 0);
+            e = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gprof[mode], graph, 0);
+        if (e == cudaSuccess) e = cudaGraphUpload(b->gprof[mode], b->stream);  // (first replay not slower)
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return cuda_fail(b, e, "profile graph");
+    }
     double acc[kStepKernels] = {};
     cudaError_t e = cudaSuccess;
     for (uint32_t s = 0; s < n && e == cudaSuccess; s++) {
-        e = launch_step_timed(b->B, b->L, b->stream, ev, b->live_on != 0);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[kStepKernels]);
+        e = cudaGraphLaunch(b->gprof[mode], b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b->prof_ev[kStepKernels]);
         for (int k = 0; k < kStepKernels && e == cudaSuccess; k++) {
             float ms = 0;
-            e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            e = cudaEventElapsedTime(&ms, b->prof_ev[k], b->prof_ev[k + 1]);
             if (k != 1 || b->L.prefix_kernel) acc[k] += ms;  // slot 1: k_tile_prefix, large grids only
         }
     }
-    for (int k = 0; k <= kStepKernels; k++) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return cuda_fail(b, e, "profile step");
     if (n) {
         b->epoch_host += n;
@@ -1293,6 +1314,10 @@ void abm_batch_destroy(abm_batch* b) {
     if (b->g8) cudaGraphExecDestroy(b->g8);
     if (b->g1_live) cudaGraphExecDestroy(b->g1_live);
     if (b->g8_live) cudaGraphExecDestroy(b->g8_live);
+    for (auto& g : b->gprof)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto& e : b->prof_ev)
+        if (e) cudaEventDestroy(e);
     if (b->own_arena && b->arena) cudaFree(b->arena);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);

@@ -1364,21 +1364,27 @@ cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool 
     return e;
 }
 
+// An event record that stays an event record when the stream is being
+// captured into a graph (abm_profile_step replays the timed step as a graph).
+static cudaError_t record_external(cudaEvent_t ev, cudaStream_t s) {
+    return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+}
+
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev, bool live) {
     const MoveKernels mk = move_kernels(L.threads_move);
-    cudaEventRecord(ev[0], s);
+    record_external(ev[0], s);
     (live ? mk.move_live : mk.move)<<<L.blocks_move, L.threads_move, 0, s>>>(B);
-    cudaEventRecord(ev[1], s);
+    record_external(ev[1], s);
     if (L.prefix_kernel) k_tile_prefix<<<1, 1024, 0, s>>>(B);
-    cudaEventRecord(ev[2], s);
+    record_external(ev[2], s);
     k_scan<<<L.blocks_scan + 1 + kSortBlocks, kThreads, 0, s>>>(B);
-    cudaEventRecord(ev[3], s);
+    record_external(ev[3], s);
     mk.scatter<<<L.blocks_scatter, L.threads_move, 0, s>>>(B);
-    cudaEventRecord(ev[4], s);
+    record_external(ev[4], s);
     k_propose<<<L.blocks_propose, kThreads, propose_smem(B), s>>>(B);
-    cudaEventRecord(ev[5], s);
+    record_external(ev[5], s);
     k_accept<<<L.blocks_accept, kThreads, 0, s>>>(B);
-    cudaEventRecord(ev[6], s);
+    record_external(ev[6], s);
     return cudaGetLastError();
 }
 

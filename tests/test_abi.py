@@ -80,16 +80,25 @@ def _bad(kind):
         m.dt_s = 10.0
     elif kind == "no_species":
         m.species = []
+    elif kind == "extent":  # 2,100,000 units of 0.1 nm: positions need 21 bits at most
+        m.compartments = [W.Compartment(W.CUBE, 210.0)]
     return m
 
 
 @pytest.mark.parametrize("kind", ["aa", "dup", "rev", "prob", "prob_neg", "radius", "product", "emit",
-                                  "comp", "child_out", "child_overlap", "dt", "huge_step"])
+                                  "comp", "child_out", "child_overlap", "dt", "huge_step", "extent"])
 def test_invalid_model_is_einval_without_device(A, kind):
     with pytest.raises(A.AbmError) as e:
         A.Sim(_bad(kind), 1)
     assert e.value.status == A.EINVAL
     assert A.arena_bytes(_bad(kind)) == 0
+
+
+def test_largest_extent_is_accepted(A):
+    """The root edge may reach 2^21 - 1 position units (209.7 um at 0.1 nm)."""
+    m = W.toy()
+    m.compartments = [W.Compartment(W.CUBE, 209.7)]
+    assert A.arena_bytes(m) > 0
 
 
 def test_cell_smaller_than_radius_is_einval(A):
