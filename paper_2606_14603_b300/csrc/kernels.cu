@@ -903,8 +903,16 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
             // order), so that a warp waits for its longest total, not for the
             // longest range of each row in turn
             const uint32_t e0 = rb[0] - ra[0], e1 = e0 + rb[1] - ra[1], e2 = e1 + rb[2] - ra[2];
-            const uint32_t total = e2 + rb[3] - ra[3];
+            // the proposer's own slot (always in one of the ranges: its cell is
+            // in its box) is left out of the sequence
+            const uint32_t self = gi >= ra[0] && gi < rb[0]   ? gi - ra[0]
+                                  : gi >= ra[1] && gi < rb[1] ? e0 + (gi - ra[1])
+                                  : gi >= ra[2] && gi < rb[2] ? e1 + (gi - ra[2])
+                                  : gi >= ra[3] && gi < rb[3] ? e2 + (gi - ra[3])
+                                                              : kNone;
+            const uint32_t total = e2 + rb[3] - ra[3] - (self != kNone ? 1u : 0u);
             auto cand = [&](uint32_t t) -> uint32_t {
+                t += t >= self;
                 return t < e0 ? ra[0] + t : t < e1 ? ra[1] + (t - e0) : t < e2 ? ra[2] + (t - e1) : ra[3] + (t - e2);
             };
             // the next candidate's record is requested while this one is examined
@@ -917,7 +925,7 @@ __device__ __forceinline__ void propose_chunk(Buffers& B, uint32_t base, uint32_
                     jn = cand(t + 1);
                     qn = pm[jn];
                 }
-                if (j != gi) consider(S, Mo, p, meta, sp, mask, rmax, ida, q, j, S.tau, best);
+                consider(S, Mo, p, meta, sp, mask, rmax, ida, q, j, S.tau, best);
             }
         } else {
             // a box wider than half a cell can meet 3 cells per axis (a cell is
