@@ -366,6 +366,22 @@ def test_edge_cases(A, oracle_mod):
     _lockstep(A, oracle_mod, m, 8, 100, dump_every=25)
 
 
+def test_positions_near_the_extent_limit(A, oracle_mod):
+    """A cube of 2,097,000 position units (209.7 um at 0.1 nm), just below the
+    2^21 that the packed record holds per axis: positions use every bit of
+    x, y and z, including those split across the record's first two words.
+    A 2.5 um contact radius makes pairs react and bind across that domain."""
+    m = W.Model("wide", [W.Species("A", 2500, 10.0), W.Species("B", 2500, 2.0), W.Species("C", 0, 1.0)],
+                [W.Reaction(0, 1, W.BIND, 2, 1, 2500.0, 1.0, 0.1)], [W.Compartment(W.CUBE, 209.7)])
+    c = _lockstep(A, oracle_mod, m, 11, 40, dump_every=10)
+    n_sp = 3
+    assert c[n_sp] > 0 or c[2] > 0                              # complexes formed or released
+    g = A.Sim(m, 11)
+    d = g.dump()
+    g.close()
+    assert d["x"].max() >= 1 << 20 and d["y"].max() >= 1 << 20 and d["z"].max() >= 1 << 20
+
+
 def test_births_overflow_is_reported_not_written(A):
     m = W.Model("flood", [W.Species("G", 20_000, 0.0, p_emit=1.0, emit=1), W.Species("P", 0, 0.0)], [],
                 [W.Compartment(W.CUBE, 2.0)])
