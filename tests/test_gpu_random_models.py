@@ -8,8 +8,9 @@ off-centre nucleus whose membrane some species may cross.  The same rules
 the library enforces (Sec. 2 inputs: species, reactions with radii and
 probabilities, compartments) bound every choice, so every model is valid.
 Each runs alone on the engine and on the oracle in lock step (digest every
-step, dump and counts at the end); then all of them share one batch and each
-member must equal its oracle run again."""
+step, dump and counts at the end); then all of them share one batch, in
+three launch shapes and grids, and each member must equal its oracle run
+again."""
 import random
 
 import numpy as np
@@ -90,12 +91,19 @@ def test_random_models_alone_equal_the_oracle(A, oracle_mod):
             o.close()
 
 
-def test_random_models_in_one_batch_equal_the_oracle(A, oracle_mod):
+# launch shapes and grids of the batch: (threads per block, CTAs per SM,
+# proposal chunk, cell edge one step above the automatic one); none may
+# change a result
+SHAPES = [(0, 0, 0, False), (128, 2, 1024, False), (512, 0, 4096, True)]
+
+
+@pytest.mark.parametrize("threads,blocks,chunk,coarse", SHAPES)
+def test_random_models_in_one_batch_equal_the_oracle(A, oracle_mod, threads, blocks, chunk, coarse):
     ms = models()
     cap = sum(int(m.n_agents * 1.5) + 4096 for m, _ in ms)
-    b = A.Batch(cap, 64 << 20, len(ms))
+    b = A.Batch(cap, 64 << 20, len(ms), blocks_per_sm=blocks, threads_per_block=threads, propose_chunk=chunk)
     try:
-        sids = [b.add(m, seed) for m, seed in ms]
+        sids = [b.add(m, seed, cell_log2=A.model_grid(m)[0] + 1 if coarse else 0) for m, seed in ms]
         b.step(STEPS)
         for (m, seed), sid in zip(ms, sids):
             o = oracle_mod.OracleSim(m, seed)
