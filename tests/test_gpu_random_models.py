@@ -114,3 +114,59 @@ def test_random_models_in_one_batch_equal_the_oracle(A, oracle_mod, threads, blo
             o.close()
     finally:
         b.close()
+
+
+def test_random_models_checkpoint_and_restore(A, oracle_mod):
+    """Half-way checkpoints of the random models restore into fresh
+    simulations that finish equal to the oracle's uninterrupted runs."""
+    for m, seed in models()[:12]:
+        g = A.Sim(m, seed)
+        g.step(STEPS // 2)
+        ck = g.checkpoint()
+        g.close()
+        rng = np.random.default_rng(seed)
+        rec = ck[0][rng.permutation(len(ck[0]))]          # records in any order
+        h = A.Sim(m, seed, restore=(rec, ck[1], ck[2]))
+        h.step(STEPS - STEPS // 2)
+        o = oracle_mod.OracleSim(m, seed)
+        o.step(STEPS)
+        try:
+            assert h.digest() == o.digest(), m.name
+            assert_same_dump(h.dump(), o.dump(), f"{m.name} restored")
+        finally:
+            h.close()
+            o.close()
+
+
+def test_random_models_admitted_and_removed_mid_run(A, oracle_mod):
+    """Members join a running batch at different steps and others leave it;
+    each member still equals the oracle run for its own number of steps."""
+    ms = models()
+    cap = sum(int(m.n_agents * 1.5) + 4096 for m, _ in ms)
+    b = A.Batch(cap, 64 << 20, len(ms))
+    steps = {}
+    sids = {}
+    try:
+        for k, (m, seed) in enumerate(ms):
+            if k % 4 == 0 and k:
+                b.step(7)                                  # members so far advance
+                for j in sids:
+                    steps[j] += 7
+            sids[k] = b.add(m, seed)
+            steps[k] = 0
+            if k % 5 == 4:                                 # an earlier member leaves
+                gone = k - 3
+                b.remove(sids.pop(gone))
+                steps.pop(gone)
+        b.step(11)
+        for j in sids:
+            steps[j] += 11
+        for k, sid in sids.items():
+            m, seed = ms[k]
+            o = oracle_mod.OracleSim(m, seed)
+            o.step(steps[k])
+            assert b.digest(sid) == o.digest(), (m.name, steps[k])
+            assert_same_dump(b.dump(sid), o.dump(), f"{m.name} after {steps[k]} steps")
+            o.close()
+    finally:
+        b.close()
