@@ -170,3 +170,21 @@ def test_random_models_admitted_and_removed_mid_run(A, oracle_mod):
             o.close()
     finally:
         b.close()
+
+
+def test_random_models_live_counts(A, oracle_mod):
+    """With live counts on, the pipelined read after every step equals the
+    oracle's counts of that step."""
+    for m, seed in models()[:12]:
+        g = A.Sim(m, seed)
+        o = oracle_mod.OracleSim(m, seed)
+        try:
+            g.live_counts(True)
+            for t in range(1, 31):
+                g.step(1)
+                g.counts_begin(t % 2)
+                o.step(1)
+                assert np.array_equal(g.counts_finish(t % 2), o.counts()), (m.name, t)
+        finally:
+            g.close()
+            o.close()
