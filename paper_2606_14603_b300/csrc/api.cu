@@ -675,7 +675,14 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     // the move and scatter passes: block size and CTAs per SM from the options
     // (the autotuner's knobs), else 256 threads and as many CTAs as fit
     const int tm = o->threads_per_block ? (int)o->threads_per_block : 256;
-    const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm(tm);
+    // above 2M agents the move pass runs in 48 registers, more warps per SM
+    // (measured: 16M agents 502 -> 486 us per step, the 64-sim sweep 0.396 ->
+    // 0.388 ms); smaller batches keep the 64-register pass, whose warps each
+    // take fewer iterations there (1M agents: the same step, 23 instead of
+    // 24.6 us in the move pass)
+    const bool large = b->cap_agents > (2ull << 20);
+    b->L.dense_move = large;
+    const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm(tm, large);
     b->L.threads_move = tm;
     b->L.blocks_move = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((b->cap_agents + tm - 1) / tm, (uint64_t)sms * per_sm));
@@ -683,7 +690,6 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     // all of its blocks that fit at once (measured: 16M agents 530 -> 512 us
     // per step); up to 2M agents the move pass's grid (the larger grid cost
     // 1M agents about 1 us)
-    const bool large = b->cap_agents > (2ull << 20);
     const uint64_t per_sm_scatter =
         o->blocks_per_sm ? o->blocks_per_sm
                          : (large ? (uint64_t)std::max(scatter_blocks_per_sm(tm), (int)per_sm) : per_sm);

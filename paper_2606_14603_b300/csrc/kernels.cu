@@ -159,7 +159,9 @@ __device__ __forceinline__ void monitor_eval(Buffers& B, uint32_t s) {
 }
 
 // Phase 1: P1 events (a released partner is moved and placed right away:
-// rare) and the move draw; issues the three table loads.
+// rare) and the move draw; issues the three table loads.  kLive: the step
+// keeps live counts (the variant of the move pass launched while they are on).
+template <bool kLive>
 __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, uint32_t parity, uint32_t i,
                                             MoveState& a) {
     uint32_t meta = (uint32_t)a.p.w;
@@ -177,26 +179,31 @@ __device__ __forceinline__ void move_phase1(Buffers& B, Ctl* ctl, uint32_t cur, 
     }
     bool alive = true, emit = false;
     if (meta & M_BOUND) {
-        const uint4 e = philox(make_uint4(a.id, t, 1u, 0u), S.key0, S.key1);
+        // A release holds its whole warp until the partner is placed, and at
+        // 1M agents that warp ends the pass: every load and reservation the
+        // release needs is requested as early as its inputs allow.  The
+        // partner id is read for every carrier (few agents are in complexes)
+        // while the release draw runs.
+        const uint32_t par = B.apar[cur][i];
         const ReactionDev& R = Mo.rx[(meta & M_RXN) >> M_RXN_SHIFT];
+        const uint4 e = philox(make_uint4(a.id, t, 1u, 0u), S.key0, S.key1);
         if ((uint64_t)e.x < R.thr_rel) {
             const bool ra = meta & M_ROLE_A;
             const int cprod = ra ? R.prod_a : R.prod_b;
             const int hprod = ra ? R.prod_b : R.prod_a;
             meta &= ~(M_BOUND | M_ROLE_A | M_RXN);
             if (hprod >= 0) {  // the partner reappears here and moves on its own
-                const uint32_t par = B.apar[cur][i];  // read only here: few agents are in complexes
+                const uint32_t k = reserve(&ctl->n_extra[parity]);  // in flight during the partner's move
                 int4 q = a.p;
                 q.w = (int)with_species(meta, (uint32_t)hprod, Mo);
                 brownian_move(S, Mo.sp[hprod], B.ztab, q, par, t);
-                const uint32_t k = reserve(&ctl->n_extra[parity]);
                 if (k < B.cap_extras) {
                     const uint32_t key = cell_of(S, q.x, q.y, q.z);
                     const uint32_t rank = atomicAdd(&B.cnt[key], 1u);
                     atomicAdd(&B.tcnt[key / kScanTile * kTileStride], 1u);
                     B.xpm[k] = repack(q, par);
                     B.xrk[k] = rank;  // the scatter finds the cell again from q
-                    if (ctl->live_counts)  // (rare: read here, not kept in registers)
+                    if (kLive)
                         atomicAdd((unsigned long long*)&live_buffer(B, ctl->epoch)[S.counts_off +
                                                                                    count_slot((uint32_t)q.w, Mo)],
                                   1ull);
@@ -353,7 +360,7 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
         a.id = (uint32_t)nx_p.w;
         if (i + 32 < wend) nx_p = pm[i + 32];
         if (i < wend) {
-            move_phase1(B, ctl, cur, parity, i, a);
+            move_phase1<kLive>(B, ctl, cur, parity, i, a);
             move_phase2(a);
         }
         const uint32_t rank = (a.flags & 1u) ? atomicAdd(&B.cnt[a.key], 1u) : 0u;
@@ -389,9 +396,12 @@ __device__ __forceinline__ void move_pass(Buffers& B, uint32_t bid, uint32_t nb)
 }
 
 // Block size TB (128, 256 or 512 threads; the autotuner's choice) with the
-// register budget of 64 per thread either way.
-template <bool kLive, int TB>
-__global__ void __launch_bounds__(TB, 1024 / TB) k_move(Buffers B) {
+// register budget of 64 per thread, or with kDense 48 (1280 threads per SM:
+// five 256-thread blocks instead of four).  More warps in flight pay on
+// large batches (16M agents: 502 -> 486 us per step); at 1M agents each warp
+// then has fewer iterations and the 64-register pass ends earlier.
+template <bool kLive, int TB, bool kDense>
+__global__ void __launch_bounds__(TB, (kDense ? 1280 : 1024) / TB) k_move(Buffers B) {
     pdl_wait();
     if (ld_volatile(&B.ctl->err)) return;
     move_pass<kLive>(B, blockIdx.x, gridDim.x);
@@ -1332,22 +1342,29 @@ size_t propose_smem(const Buffers& B) { return 4 * ((size_t)B.propose_chunk + B.
 
 namespace {
 using StepKernel = void (*)(Buffers);
-// k_move (without, with live counts) and k_scatter for a block size
+// k_move (without, with live counts) and k_scatter for a block size and
+// register budget
 struct MoveKernels {
     StepKernel move, move_live, scatter;
 };
-MoveKernels move_kernels(int threads) {
-    if (threads == 128) return {k_move<false, 128>, k_move<true, 128>, k_scatter<128>};
-    if (threads == 512) return {k_move<false, 512>, k_move<true, 512>, k_scatter<512>};
-    return {k_move<false, 256>, k_move<true, 256>, k_scatter<256>};
+MoveKernels move_kernels(int threads, bool dense) {
+    if (threads == 128)
+        return dense ? MoveKernels{k_move<false, 128, true>, k_move<true, 128, true>, k_scatter<128>}
+                     : MoveKernels{k_move<false, 128, false>, k_move<true, 128, false>, k_scatter<128>};
+    if (threads == 512)
+        return dense ? MoveKernels{k_move<false, 512, true>, k_move<true, 512, true>, k_scatter<512>}
+                     : MoveKernels{k_move<false, 512, false>, k_move<true, 512, false>, k_scatter<512>};
+    return dense ? MoveKernels{k_move<false, 256, true>, k_move<true, 256, true>, k_scatter<256>}
+                 : MoveKernels{k_move<false, 256, false>, k_move<true, 256, false>, k_scatter<256>};
 }
 }  // namespace
 
 bool valid_move_threads(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 
-int move_blocks_per_sm(int threads) {
+int move_blocks_per_sm(int threads, bool dense) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, move_kernels(threads).move, threads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, move_kernels(threads, dense).move, threads, 0) !=
+            cudaSuccess ||
         n < 1)
         n = 1024 / threads;
     return n;
@@ -1355,14 +1372,15 @@ int move_blocks_per_sm(int threads) {
 
 int scatter_blocks_per_sm(int threads) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, move_kernels(threads).scatter, threads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, move_kernels(threads, false).scatter, threads, 0) !=
+            cudaSuccess ||
         n < 1)
         n = 1024 / threads;
     return n;
 }
 
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool live) {
-    const MoveKernels mk = move_kernels(L.threads_move);
+    const MoveKernels mk = move_kernels(L.threads_move, L.dense_move);
     cudaError_t e = launch_pdl(live ? mk.move_live : mk.move, L.blocks_move, s, B, 0, L.threads_move);
     if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1 + kSortBlocks, s, B);
@@ -1379,7 +1397,7 @@ static cudaError_t record_external(cudaEvent_t ev, cudaStream_t s) {
 }
 
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev, bool live) {
-    const MoveKernels mk = move_kernels(L.threads_move);
+    const MoveKernels mk = move_kernels(L.threads_move, L.dense_move);
     record_external(ev[0], s);
     (live ? mk.move_live : mk.move)<<<L.blocks_move, L.threads_move, 0, s>>>(B);
     record_external(ev[1], s);
