@@ -677,9 +677,9 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     const int tm = o->threads_per_block ? (int)o->threads_per_block : 256;
     // above 2M agents the move pass runs in 48 registers, more warps per SM
     // (measured: 16M agents 502 -> 486 us per step, the 64-sim sweep 0.396 ->
-    // 0.388 ms); smaller batches keep the 64-register pass, whose warps each
-    // take fewer iterations there (1M agents: the same step, 23 instead of
-    // 24.6 us in the move pass)
+    // 0.388 ms); smaller batches keep the 64-register pass, measured faster
+    // there (1M agents: the same step, 22.5-23 instead of 24.6 us in the
+    // move pass)
     const bool large = b->cap_agents > (2ull << 20);
     b->L.dense_move = large;
     const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm(tm, large);
