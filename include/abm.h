@@ -144,7 +144,9 @@ typedef struct {
                                         on an SM at once */
     /* Launch shape (an autotuner's knobs; no choice changes a result): */
     uint32_t       threads_per_block;/* block size of the move and scatter
-                                        kernels: 128, 256 or 512; 0 = 256    */
+                                        kernels: 128, 256 or 512; 0 = 128
+                                        for capacities from 2^20 to 2^21
+                                        agents, else 256                     */
     uint32_t       propose_chunk;    /* sorted agents per block of the
                                         proximity search (a block covers
                                         several small simulations or part of a

@@ -34,7 +34,7 @@ class Choice:
     blocks_per_sm: int       # 0 = the CTAs of the move pass that fit on an SM at once
     ms_per_step: float
     groups: int = 1          # batches stepped concurrently, one CUDA stream each
-    threads_per_block: int = 0   # move / scatter block size, 0 = 256
+    threads_per_block: int = 0   # move / scatter block size, 0 = the library default (128 from 1M to 2M agents of capacity, else 256)
     propose_chunk: int = 0       # sorted agents per proximity-search block, 0 = by capacity
 
     def key(self):

@@ -673,19 +673,28 @@ abm_status abm_batch_create(const abm_batch_options* o, abm_batch** out) {
     b->L.blocks_agents =
         (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * (uint64_t)move_blocks_per_sm(256)));
     // the move and scatter passes: block size and CTAs per SM from the options
-    // (the autotuner's knobs), else 256 threads and as many CTAs as fit
-    const int tm = o->threads_per_block ? (int)o->threads_per_block : 256;
-    // above 2M agents the move pass runs in 48 registers, more warps per SM
-    // (measured: 16M agents 502 -> 486 us per step, the 64-sim sweep 0.396 ->
-    // 0.388 ms); smaller batches keep the 64-register pass, measured faster
-    // there (1M agents: the same step, 22.5-23 instead of 24.6 us in the
-    // move pass)
+    // (the autotuner's knobs), else as many CTAs as fit, of 128 threads for
+    // capacities from 1M to 2M agents and of 256 otherwise: the move pass's 56
+    // registers fit nine 128-thread blocks per SM (36 warps) where 256-thread
+    // blocks fit four (32 warps); measured 2.4-3.2% faster steps at 1M and
+    // 1.5M agents, within +-1.4% (either way) from 50k to 700k.  Above 2M
+    // agents the move pass runs in 48 registers, more warps per SM (measured:
+    // 16M agents 502 -> 486 us per step, the 64-sim sweep 0.396 -> 0.388 ms);
+    // smaller batches keep the 64-register pass, measured faster there (1M
+    // agents: the same step, 22.5-23 instead of 24.6 us in the move pass)
     const bool large = b->cap_agents > (2ull << 20);
+    const int tm = o->threads_per_block ? (int)o->threads_per_block
+                                        : (!large && b->cap_agents >= (1ull << 20) ? 128 : 256);
     b->L.dense_move = large;
     const uint64_t per_sm = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm(tm, large);
     b->L.threads_move = tm;
     b->L.blocks_move = (int)std::max<uint64_t>(
         1, std::min<uint64_t>((b->cap_agents + tm - 1) / tm, (uint64_t)sms * per_sm));
+    // the live-counting variant holds more registers: its own resident grid
+    // (with the other's, 128-thread blocks would leave a second wave)
+    const uint64_t per_sm_live = o->blocks_per_sm ? o->blocks_per_sm : (uint64_t)move_blocks_per_sm(tm, large, true);
+    b->L.blocks_move_live = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((b->cap_agents + tm - 1) / tm, (uint64_t)sms * per_sm_live));
     // the scatter needs fewer registers than the move pass: on large batches
     // all of its blocks that fit at once (measured: 16M agents 530 -> 512 us
     // per step); up to 2M agents the move pass's grid (the larger grid cost

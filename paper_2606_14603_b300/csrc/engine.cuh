@@ -333,6 +333,7 @@ __device__ __forceinline__ bool mon_due(const MonDev& M, uint32_t t) {
 struct Launch {
     int blocks_agents;       // grid of the between-step per-agent kernels (grid-stride, 256 threads)
     int blocks_move;         // grid of k_move: the blocks of threads_move that fit at once
+    int blocks_move_live;    // the same for its live-counting variant (more registers, maybe fewer blocks)
     int blocks_scatter;      // grid of k_scatter (same block size): the blocks that fit at once
     int threads_move;        // block size of k_move and k_scatter: 128, 256 or 512
     bool dense_move;         // k_move in 48 registers (five 256-thread blocks per SM): batches above 2M agents
@@ -344,9 +345,9 @@ struct Launch {
 };
 
 // CTAs of k_move with `threads` threads that fit on one SM at once (its
-// registers decide; dense: the 48-register variant); valid block sizes are
-// 128, 256 and 512.
-int move_blocks_per_sm(int threads, bool dense = false);
+// registers decide; dense: the 48-register variant; live: the variant that
+// keeps live counts); valid block sizes are 128, 256 and 512.
+int move_blocks_per_sm(int threads, bool dense = false, bool live = false);
 int scatter_blocks_per_sm(int threads);
 bool valid_move_threads(int threads);
 size_t propose_smem(const Buffers& B);

@@ -1361,9 +1361,10 @@ MoveKernels move_kernels(int threads, bool dense) {
 
 bool valid_move_threads(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 
-int move_blocks_per_sm(int threads, bool dense) {
+int move_blocks_per_sm(int threads, bool dense, bool live) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, move_kernels(threads, dense).move, threads, 0) !=
+    const MoveKernels mk = move_kernels(threads, dense);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, live ? mk.move_live : mk.move, threads, 0) !=
             cudaSuccess ||
         n < 1)
         n = 1024 / threads;
@@ -1381,7 +1382,8 @@ int scatter_blocks_per_sm(int threads) {
 
 cudaError_t launch_step(const Buffers& B, const Launch& L, cudaStream_t s, bool live) {
     const MoveKernels mk = move_kernels(L.threads_move, L.dense_move);
-    cudaError_t e = launch_pdl(live ? mk.move_live : mk.move, L.blocks_move, s, B, 0, L.threads_move);
+    cudaError_t e =
+        launch_pdl(live ? mk.move_live : mk.move, live ? L.blocks_move_live : L.blocks_move, s, B, 0, L.threads_move);
     if (e == cudaSuccess && L.prefix_kernel) e = launch_pdl(k_tile_prefix, 1, s, B, 0, 1024);
     if (e == cudaSuccess) e = launch_pdl(k_scan, L.blocks_scan + 1 + kSortBlocks, s, B);
     if (e == cudaSuccess) e = launch_pdl(mk.scatter, L.blocks_scatter, s, B, 0, L.threads_move);
@@ -1399,7 +1401,7 @@ static cudaError_t record_external(cudaEvent_t ev, cudaStream_t s) {
 cudaError_t launch_step_timed(const Buffers& B, const Launch& L, cudaStream_t s, cudaEvent_t* ev, bool live) {
     const MoveKernels mk = move_kernels(L.threads_move, L.dense_move);
     record_external(ev[0], s);
-    (live ? mk.move_live : mk.move)<<<L.blocks_move, L.threads_move, 0, s>>>(B);
+    (live ? mk.move_live : mk.move)<<<live ? L.blocks_move_live : L.blocks_move, L.threads_move, 0, s>>>(B);
     record_external(ev[1], s);
     if (L.prefix_kernel) k_tile_prefix<<<1, 1024, 0, s>>>(B);
     record_external(ev[2], s);
