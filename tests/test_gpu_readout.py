@@ -171,3 +171,28 @@ def test_live_counts_with_a_frozen_simulation(A):
                 frozen = got if frozen is None else frozen
                 assert np.array_equal(got, frozen), k
     bt.close()
+
+
+@pytest.mark.parametrize("n", [1_200_000, 2_600_000])
+def test_live_counts_on_the_large_launch_shapes(A, n):
+    """Capacities of 1M to 2M agents run the move pass in 128-thread blocks
+    (its live-counting variant on a resident grid of its own), larger ones
+    in its 48-register variant: with live counts on, the counts after every
+    step equal the counting pass, and the trajectory equals the same
+    simulation's without live counts."""
+    m = W.mapk(n)
+    g = A.Sim(m, 7)
+    h = A.Sim(m, 7)
+    try:
+        g.live_counts(True)
+        for t in range(1, 9):
+            g.step(1)
+            h.step(1)
+            g.counts_begin(t % 2)
+            live = g.counts_finish(t % 2)
+            assert np.array_equal(live, g.counts()), (n, t)
+        assert g.digest() == h.digest()
+        assert np.array_equal(g.counts(), h.counts())
+    finally:
+        g.close()
+        h.close()
